@@ -1,0 +1,483 @@
+"""Benchmark: the site-local lattice-expression hot path on one GB300 per rank.
+
+One step = one pass of every hot-path row over synthetic inputs of the 48^4
+volume-sweep configuration (5,308,416 sites):
+  A2 z=a*b (FP64 storage), A3 z=a*v, A4 Lorentz z_mu=a_mu*b_mu (mu=0..3),
+  A5 fused z=a*b+c*d, z=a*b*c+0.5*d, z=adj(a)*b-b*adj(a),
+  A6 z=a*b stored in FP32 / BF16 / FP16 (FP32 accumulation),
+  A7 z=a*b in two-row (12-real) SU(3) storage, FP64 and FP32,
+  A8 64 lattices of mixed volumes, z=a*b+c*d each, one CUDA-graph launch,
+  A9 reverse mode of z=a*b and of z=a*b+c*d.
+`value` is the aggregate algorithmic bandwidth of the step (STREAM
+convention: every input read once, every output written once) with inputs
+resident in HBM; every field is larger than the 129 MB L2, so no flush is
+needed between steps.  `e2e` runs the same step through the C ABI from pinned
+host buffers (upload + pack, evaluate, unpack + download inside the timed
+region).  `--impl reference` times the CPU oracle on a bounded sample.
+
+Multi-GPU (torchrun): every rank runs its own copy of the step (independent
+lattices, no collective on the data path); value = total bytes of all ranks /
+max time over ranks (weak scaling).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("SU(3)xSU(3) stream GB/s & sites/s, % HBM peak; FP64 vs reduced-prec at stated error")
+DIMS = (48, 48, 48, 48)
+SEED = 1710094090 + 1
+BATCH_SHAPES = [(4, 4, 4, 4), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 24)]
+
+# algorithmic bytes per site (inputs read once, outputs written once)
+B_MM, B_MV, B_E1, B_E2, B_E3 = 432, 240, 720, 720, 432
+B_F32, B_H, B_C12, B_C12F = 216, 108, 288, 144
+B_ADJ_MM, B_ADJ_E1 = 720, 1296
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows),
+                "power_w_max": max([float(r[2]) for r in self.rows
+                                    if r[2].replace(".", "").isdigit()] or [0.0])}
+
+
+# ------------------------------------------------------------------ rows
+class Row:
+    def __init__(self, name, nbytes, sites, run, inputs, outputs, launches=1, dtype="f64"):
+        self.name, self.nbytes, self.sites, self.run = name, nbytes, sites, run
+        self.inputs, self.outputs, self.launches, self.dtype = inputs, outputs, launches, dtype
+        self.ms = []
+
+
+def build_rows(su3s, synth, torch, with_host):
+    """Allocate fields, fill them from the seeded generator, return the rows."""
+    v = synth.volume(DIMS)
+    lat = su3s.Lattice(DIMS)
+    F64, MATRIX, VECTOR = su3s.F64, su3s.MATRIX, su3s.VECTOR
+    host = {}
+
+    def gen(kind, field, n, nmu=1, dims=None, seed=SEED):
+        if kind == "su3":
+            arr = synth.su3(seed, field, n * nmu)
+        elif kind == "gm":
+            arr = synth.gauss_matrix(seed, field, n * nmu)
+        else:
+            arr = synth.gauss_vector(seed, field, n * nmu)
+        return arr
+
+    def pinned(arr):
+        t = torch.from_numpy(arr.reshape(-1))
+        return t.pin_memory() if with_host else None
+
+    def field(lat_, kind, nmu, prec, arr):
+        f = su3s.Field(lat_, kind, nmu, prec, su3s.SOA)
+        f.upload(arr)
+        return f
+
+    H = {}
+    for n, fid in (("a", 0), ("b", 1), ("c", 2), ("d", 3)):
+        H[n] = gen("su3", fid, v)
+    H["v"] = gen("vec", 4, v)
+    H["w"] = gen("gm", 5, v)
+    H["la"] = gen("su3", 0, v, 4)
+    H["lb"] = gen("su3", 1, v, 4)
+    P = {k: pinned(a) for k, a in H.items()}
+
+    def fields_for(prec, names=("a", "b", "c", "d")):
+        return {n: field(lat, MATRIX, 1, prec, H[n]) for n in names}
+
+    Fd = fields_for(F64)
+    Fv = field(lat, VECTOR, 1, F64, H["v"])
+    Fw = field(lat, MATRIX, 1, F64, H["w"])
+    La, Lb = field(lat, MATRIX, 4, F64, H["la"]), field(lat, MATRIX, 4, F64, H["lb"])
+    rows = []
+
+    shared_out = {}
+
+    def out_pin(f):
+        # outputs of equal size share one pinned buffer (downloads are stream-ordered)
+        n = int(np.prod(f.canonical_shape))
+        if not with_host:
+            return None
+        if n not in shared_out:
+            shared_out[n] = torch.empty(n, dtype=torch.float64).pin_memory()
+        return shared_out[n]
+
+    def mk(name, bps, dest, expr, ins, dtype="f64"):
+        def run(stream, dest=dest, expr=expr):
+            su3s.evaluate(dest, expr, su3s.MATH_DEFAULT, stream)
+            return 1
+        return Row(name, bps * v * dest.nmu, v * dest.nmu, run, ins, [(dest, out_pin(dest))],
+                   dtype=dtype)
+
+    z = Fd["a"].like()
+    rows.append(mk("A2 z=a*b", B_MM, z, Fd["a"] * Fd["b"],
+                   [(Fd["a"], P["a"]), (Fd["b"], P["b"])]))
+    zv = Fv.like()
+    rows.append(mk("A3 z=a*v", B_MV, zv, Fd["a"] * Fv, [(Fd["a"], P["a"]), (Fv, P["v"])]))
+    zl = La.like()
+    rows.append(mk("A4 z_mu=a_mu*b_mu", B_MM, zl, La * Lb, [(La, P["la"]), (Lb, P["lb"])]))
+    z1, z2, z3 = Fd["a"].like(), Fd["a"].like(), Fd["a"].like()
+    a, b, c, d = (Fd[n] for n in "abcd")
+    rows.append(mk("A5 z=a*b+c*d", B_E1, z1, a * b + c * d,
+                   [(Fd[n], P[n]) for n in "abcd"]))
+    rows.append(mk("A5 z=a*b*c+0.5*d", B_E2, z2, a * b * c + 0.5 * d,
+                   [(Fd[n], P[n]) for n in "abcd"]))
+    rows.append(mk("A5 z=adj(a)*b-b*adj(a)", B_E3, z3, a.adj() * b - b * a.adj(),
+                   [(Fd[n], P[n]) for n in "ab"]))
+    for prec, nm, bps in ((su3s.F32, "f32", B_F32), (su3s.BF16, "bf16", B_H), (su3s.F16, "f16", B_H),
+                          (su3s.F64_C12, "f64_c12", B_C12), (su3s.F32_C12, "f32_c12", B_C12F)):
+        Fp = fields_for(prec, ("a", "b"))
+        zp = Fp["a"].like()
+        tag = "A7" if "c12" in nm else "A6"
+        rows.append(mk("%s z=a*b %s" % (tag, nm), bps, zp, Fp["a"] * Fp["b"],
+                       [(Fp["a"], P["a"]), (Fp["b"], P["b"])], dtype=nm))
+
+    # A8: 64 lattices of mixed volumes, one graph launch
+    picks = (synth.uniform_real(SEED + 3, 40, 64) + 1.0) / 2.0 * len(BATCH_SHAPES)
+    batch = su3s.Batch()
+    bins, bouts, bsites = [], [], 0
+    keep = []
+    for i, p in enumerate(picks):
+        dims = BATCH_SHAPES[min(int(p), len(BATCH_SHAPES) - 1)]
+        bl = su3s.Lattice(dims)
+        nv = synth.volume(dims)
+        fs = {}
+        for n in "abcd":
+            arr = synth.su3(SEED + 3 + 1000 * i, synth.FIELD[n], nv)
+            fs[n] = field(bl, MATRIX, 1, F64, arr)
+            bins.append((fs[n], pinned(arr)))
+        zb = fs["a"].like()
+        batch.add(zb, fs["a"] * fs["b"] + fs["c"] * fs["d"])
+        bouts.append((zb, out_pin(zb)))
+        bsites += nv
+        keep.append((bl, fs, zb))
+    batch.build()
+
+    def run_batch(stream):
+        batch.launch(stream)
+        return 1
+    rows.append(Row("A8 batch 64 lattices z=a*b+c*d", B_E1 * bsites, bsites, run_batch, bins, bouts))
+    rows[-1].keep = (batch, keep)
+
+    # A9: reverse mode
+    ga, gb = a.like(), a.like()
+
+    def run_adj(stream):
+        su3s.eval_adjoint(a * b, Fw, [ga, gb], su3s.MATH_DEFAULT, stream)
+        return 1
+    rows.append(Row("A9 adjoint of z=a*b", B_ADJ_MM * v, v, run_adj,
+                    [(a, P["a"]), (b, P["b"]), (Fw, P["w"])],
+                    [(ga, out_pin(ga)), (gb, out_pin(gb))]))
+    g4 = [a.like() for _ in range(4)]
+    e1 = a * b + c * d
+
+    def run_adj1(stream):
+        su3s.eval_adjoint(e1, Fw, g4, su3s.MATH_DEFAULT, stream)
+        return 1
+    rows.append(Row("A9 adjoint of z=a*b+c*d", B_ADJ_E1 * v, v, run_adj1,
+                    [(Fd[n], P[n]) for n in "abcd"] + [(Fw, P["w"])],
+                    [(g, out_pin(g)) for g in g4]))
+    return rows, {"lat": lat, "fields": (Fd, Fv, Fw, La, Lb), "host": H}
+
+
+def time_step(rows, torch, stream, steps, warmup, per_row_events=True):
+    """Run `steps` steps; return (total ms from the outer events, per-row ms lists)."""
+    for _ in range(warmup):
+        for r in rows:
+            r.run(stream)
+    stream.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in rows] for _ in range(steps)] if per_row_events else None
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    start.record(stream)
+    for k in range(steps):
+        for i, r in enumerate(rows):
+            if ev:
+                ev[k][i][0].record(stream)
+            launches += r.run(stream)
+            if ev:
+                ev[k][i][1].record(stream)
+    end.record(stream)
+    end.synchronize()
+    total = start.elapsed_time(end)
+    per_row = [[ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(steps)] for i in range(len(rows))] \
+        if ev else None
+    return total, per_row, launches
+
+
+def time_e2e(rows, torch, stream, steps):
+    def one():
+        for r in rows:
+            for f, h in r.inputs:
+                f.upload(h, stream)
+            r.run(stream)
+            for f, h in r.outputs:
+                f.download(out=h, stream=stream)
+    one()
+    stream.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        one()
+    end.record(stream)
+    end.synchronize()
+    h2d = sum(h.numel() * 8 for r in rows for _, h in r.inputs)
+    d2h = sum(h.numel() * 8 for r in rows for _, h in r.outputs)
+    return start.elapsed_time(end) / steps, h2d, d2h
+
+
+# ----------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(budget_s=12.0, frac_sites=1 << 16):
+    """The oracle, as it stands (single-threaded C), on a bounded sample of the
+    step: every row's computation on the first `frac_sites` sites."""
+    import oracle
+    import synth
+    n = frac_sites
+    a, b, c, d = (synth.su3(SEED, i, n) for i in range(4))
+    vv = synth.gauss_vector(SEED, 4, n)
+    w = synth.gauss_matrix(SEED, 5, n)
+    la, lb = synth.su3(SEED, 0, 4 * n), synth.su3(SEED, 1, 4 * n)
+    leaves = {"a": a, "b": b, "c": c, "d": d}
+    E1 = ("add", ("mul", ("leaf", "a"), ("leaf", "b")), ("mul", ("leaf", "c"), ("leaf", "d")))
+    E2 = ("add", ("mul", ("mul", ("leaf", "a"), ("leaf", "b")), ("leaf", "c")),
+          ("scale", 0.5, ("leaf", "d")))
+    E3 = ("sub", ("mul", ("adj", ("leaf", "a")), ("leaf", "b")),
+          ("mul", ("leaf", "b"), ("adj", ("leaf", "a"))))
+    MM = ("mul", ("leaf", "a"), ("leaf", "b"))
+    bytes_one = n * (B_MM + B_MV + 4 * B_MM + B_E1 + B_E2 + B_E3 + B_F32 + 2 * B_H + B_C12 + B_C12F
+                     + B_E1 + B_ADJ_MM + B_ADJ_E1)
+
+    def one_pass():
+        oracle.mm(a, b)
+        oracle.mv(a, vv)
+        oracle.mm(la, lb)
+        oracle.eval_tree(E1, leaves)
+        oracle.eval_tree(E2, leaves)
+        oracle.eval_tree(E3, leaves)
+        for fmt in ("f32", "bf16", "f16"):
+            oracle.round_to(oracle.mm(oracle.round_to(a, fmt), oracle.round_to(b, fmt)), fmt)
+        for fmt in (None, "f32"):
+            ra = a[:, :2].copy() if fmt is None else oracle.round_to(a[:, :2].copy(), fmt)
+            rb = b[:, :2].copy() if fmt is None else oracle.round_to(b[:, :2].copy(), fmt)
+            oracle.mm(oracle.c12_expand(ra), oracle.c12_expand(rb))
+        oracle.eval_tree(E1, leaves)   # the batched row: same tree
+        oracle.eval_adjoint(MM, leaves, w)
+        oracle.eval_adjoint(E1, leaves, w)
+
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        one_pass()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": bytes_one * reps / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "every row of the step on the first %d sites (%d passes, %.1f s)"
+                      % (n, reps, el),
+            "seconds": el, "passes": reps, "bytes_per_pass": bytes_one}
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w_s = 2.0
+        k_s = min(25.0, max(5.0, 2.0 * args.steps))
+        for _ in range(args.warmup):
+            cpu_oracle_sample(budget_s=w_s / max(1, args.warmup), frac_sites=1 << 14)
+        cb = cpu_oracle_sample(budget_s=k_s, frac_sites=1 << 16)
+        line = {"impl": "reference", "metric": METRIC, "value": round(cb["value"], 4),
+                "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "48^4 lattice, every hot-path row (A2-A9), CPU oracle on a "
+                                       "bounded sample of sites"},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": round(cb["value"], 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1710_09409_gb300 as su3s
+    import synth
+    su3s.load()
+    stream = torch.cuda.Stream()
+    with_host = not args.no_e2e
+    rows, keep = build_rows(su3s, synth, torch, with_host)
+    torch.cuda.synchronize()
+
+    # device-resident timing
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    total_ms, per_row, launches = time_step(rows, torch, stream, args.steps, args.warmup)
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    bytes_step = sum(r.nbytes for r in rows)
+    value = bytes_step * ws / (ms_step * 1e-3) / 1e9
+
+    row_out = []
+    for r, ms in zip(rows, per_row):
+        m = float(np.mean(ms))
+        row_out.append({"row": r.name, "dtype": r.dtype, "ms": round(m, 5),
+                        "GB_s": round(r.nbytes / (m * 1e-3) / 1e9, 1),
+                        "Gsites_s": round(r.sites / (m * 1e-3) / 1e9, 3)})
+    peak, peak_kind = read_peaks()
+    # dominant kernel: the largest share of the step time
+    di = int(np.argmax([np.mean(ms) for ms in per_row]))
+    dm = float(np.mean(per_row[di]))
+    achieved = rows[di].nbytes / (dm * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": rows[di].name, "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6800 GB/s", "traffic": None,
+            "algorithmic_bytes_per_launch": rows[di].nbytes}
+    a2 = row_out[0]
+
+    # native FP64 arithmetic for the FP64 rows, reported beside (not in the step)
+    variants = []
+    su3s.set_default_math(su3s.MATH_F64)
+    for r in rows:
+        if r.dtype == "f64" and not r.name.startswith("A8"):
+            _, pr, _ = time_step([r], torch, stream, 20, 2)
+            m = float(np.mean(pr[0]))
+            variants.append({"row": r.name, "math": "native f64", "ms": round(m, 5),
+                             "GB_s": round(r.nbytes / (m * 1e-3) / 1e9, 1)})
+    su3s.set_default_math(su3s.MATH_DF32)
+
+    e2e = None
+    if with_host:
+        e_ms, h2d, d2h = time_e2e(rows, torch, stream, args.e2e_steps)
+        if dist:
+            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": round(bytes_step * ws / (e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 3)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_sample()
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "48^4 lattice (5,308,416 sites), every hot-path row A2-A9 once per "
+                                   "step; FP64 rows in the library default arithmetic (df32)",
+                       "lattice": list(DIMS), "layout": "soa",
+                       "l2": "every field larger than the 129 MB L2; no flush needed",
+                       "bytes_per_step": bytes_step, "seed": SEED},
+            "sites_per_s": round(a2["Gsites_s"] * 1e9 * ws, 0),
+            "rows": row_out, "f64_native_rows": variants,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

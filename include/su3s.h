@@ -1,0 +1,299 @@
+/*
+ * su3s -- site-local evaluation of lattice expressions on one GB300 GPU.
+ *
+ * C ABI.  No C++ or framework types cross this boundary: only plain integers,
+ * doubles, host or device pointers, sizes and opaque handles.  A stream
+ * argument is a cudaStream_t passed as void* (NULL = the legacy default
+ * stream).  Every call returns an int status (SU3S_OK = 0); on failure
+ * su3s_last_error() returns a message for the calling thread.  No call aborts
+ * the process or throws.
+ *
+ * The objects follow arXiv:1710.09409:
+ *   - a lattice is a 4-d Cartesian grid Lx*Ly*Lz*Lt (Sec. 3, Listing 2:
+ *     Lattice<T> v(&grid); Sec. 4, Listing 3);
+ *   - a field is a lattice-wide array of site objects: complex 3x3 colour
+ *     matrices (Su3f in Sec. 4), complex colour vectors, or reals
+ *     (Lattice<double>, Listing 2), optionally with `nmu` objects per site
+ *     (Lorentz-indexed link fields, nmu = 4);
+ *   - an expression is a tree of products, sums, differences, real scalings
+ *     and Hermitian adjoints of fields (the expression-template engine of
+ *     Sec. 3, Listing 1), and evaluating it into a destination field computes
+ *     _odata[ss] = eval(ss, expr) for every site ss in one pass.
+ *
+ * Canonical host layout ("canonical AoS"): double[V][nmu][w] with
+ * w = 18 (matrix: row, column, re/im), 6 (vector) or 1 (real), site index
+ * x + Lx*(y + Ly*(z + Lz*t)).  Device layouts are described at
+ * su3s_field_bytes.
+ */
+#ifndef SU3S_H
+#define SU3S_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SU3S_OK 0
+#define SU3S_EINVAL 1       /* bad argument: null handle, value out of range      */
+#define SU3S_ETYPE 2        /* ill-typed expression (e.g. vector * matrix)        */
+#define SU3S_ESHAPE 3       /* fields disagree in lattice, links, layout or size  */
+#define SU3S_ENOMEM 4       /* an allocation made by the library failed           */
+#define SU3S_ECUDA 5        /* a CUDA call failed; the message names it           */
+#define SU3S_EUNSUPPORTED 6 /* well-formed request this library does not handle   */
+
+/* ---- field kinds ---- */
+#define SU3S_MATRIX 0 /* complex 3x3 colour matrix */
+#define SU3S_VECTOR 1 /* complex colour 3-vector   */
+#define SU3S_REAL 2   /* one real per site object   */
+
+/* ---- storage precisions ---- */
+#define SU3S_F64 0     /* complex: 2 x FP64                                            */
+#define SU3S_F32 1     /* complex: 2 x FP32 (round to nearest even on store)          */
+#define SU3S_BF16 2    /* complex: 2 x BF16                                            */
+#define SU3S_F16 3     /* complex: 2 x FP16                                            */
+#define SU3S_F64_C12 4 /* SU(3) matrix as rows 0,1 only (12 FP64); row 2 rebuilt      */
+#define SU3S_F32_C12 5 /* SU(3) matrix as rows 0,1 only (12 FP32); row 2 rebuilt      */
+
+/* ---- device layouts ---- */
+#define SU3S_SOA 0   /* component-major: [mu][component][Vpad]                      */
+#define SU3S_AOSOA 1 /* site-blocked:    [Vpad/B][mu][component][B], B = block      */
+
+/* ---- arithmetic used for FP64 storage ---- */
+#define SU3S_MATH_DEFAULT 0 /* the library default (see su3s_set_default_math)     */
+#define SU3S_MATH_F64 1     /* native IEEE FP64 with fused multiply-add              */
+#define SU3S_MATH_DF32 2    /* FP64-accurate pair-of-FP32 arithmetic (see below)     */
+
+typedef struct su3s_lattice su3s_lattice;
+typedef struct su3s_field su3s_field;
+typedef struct su3s_expr su3s_expr;
+typedef struct su3s_batch su3s_batch;
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next call on the same thread. */
+const char* su3s_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int su3s_version(void);
+
+/* ------------------------------------------------------------------------
+ * Lattice (Sec. 3, Listing 2 / Sec. 4, Listing 3: the grid that fields live on)
+ * ---------------------------------------------------------------------- */
+
+/* Create a lattice of lx*ly*lz*lt sites.  Each extent must be >= 1 and the
+ * volume must be < 2^31.  *out receives a handle owned by the caller.
+ * EINVAL on a bad extent or null out. */
+int su3s_lattice_create(int lx, int ly, int lz, int lt, su3s_lattice** out);
+
+/* Destroy a lattice handle.  Fields keep their own copy of the geometry, so a
+ * lattice may be destroyed while fields made from it live on.  NULL is a
+ * no-op. */
+int su3s_lattice_destroy(su3s_lattice* lat);
+
+/* Number of sites of a lattice in *out.  EINVAL on null arguments. */
+int su3s_lattice_volume(const su3s_lattice* lat, int64_t* out);
+
+/* ------------------------------------------------------------------------
+ * Fields (lattice-wide arrays of site objects)
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of device memory a field needs, in *bytes.
+ *   kind   SU3S_MATRIX / SU3S_VECTOR / SU3S_REAL
+ *   nmu    objects per site, 1..8 (4 for Lorentz-indexed link fields)
+ *   prec   SU3S_F64 ... SU3S_F32_C12 (C12 only for matrices; reals only F64)
+ *   layout SU3S_SOA or SU3S_AOSOA
+ *   block  B for SU3S_AOSOA: a power of two, 4..1024; ignored for SU3S_SOA
+ * The volume is padded to Vpad (a multiple of 64 for SOA, of max(B,4) for
+ * AOSOA).  With ncomp complex components per object (9 matrix, 6 two-row
+ * matrix, 3 vector) the element at (site s, link mu, component c) is at
+ *   SOA:   (mu*ncomp + c)*Vpad + s
+ *   AOSOA: ((s/B)*nmu + mu)*ncomp*B + c*B + s%B
+ * in units of one complex (reals: one real, ncomp = 1). */
+int su3s_field_bytes(const su3s_lattice* lat, int kind, int nmu, int prec, int layout, int block,
+                     size_t* bytes);
+
+/* Wrap caller-owned device memory as a field.  dev_ptr must be 16-byte
+ * aligned and hold at least su3s_field_bytes(...) bytes; the library never
+ * frees it, and the memory must outlive the handle and every queued kernel
+ * that uses it.  The contents are not touched.  *out receives a handle owned
+ * by the caller.  EINVAL on a bad argument or alignment, ESHAPE if bytes is
+ * too small, EUNSUPPORTED for a kind/precision pair that has no storage. */
+int su3s_field_wrap(const su3s_lattice* lat, int kind, int nmu, int prec, int layout, int block,
+                    void* dev_ptr, size_t bytes, su3s_field** out);
+
+/* Destroy a field handle (the wrapped memory is untouched).  NULL is a no-op. */
+int su3s_field_destroy(su3s_field* f);
+
+/* Pack (Grid's vector layout, Sec. 5, done once on the device): read the
+ * canonical AoS FP64 array at dev_canonical (device memory, V*nmu*w doubles)
+ * and write the field in its device layout and precision, rounding to
+ * nearest-even for FP32/BF16/FP16 and keeping rows 0,1 for the C12 formats.
+ * Pad sites are set to zero.  Asynchronous on `stream`. */
+int su3s_field_pack(su3s_field* f, const double* dev_canonical, void* stream);
+
+/* Unpack: write the canonical AoS FP64 array (V*nmu*w doubles, device memory)
+ * from the field, widening reduced precisions exactly and rebuilding row 2 of
+ * C12 matrices as conj(row0 x row1).  Asynchronous on `stream`. */
+int su3s_field_unpack(const su3s_field* f, double* dev_canonical, void* stream);
+
+/* Upload from host memory: copy n_doubles (must equal V*nmu*w) canonical AoS
+ * doubles from host_canonical to a device staging buffer and pack it into the
+ * field.  The staging buffer is allocated and freed by the library in stream
+ * order (cudaMallocAsync / cudaFreeAsync).  Pinned host memory makes the copy
+ * asynchronous; the host buffer must not change until the stream reaches
+ * this point.  ESHAPE if n_doubles is wrong, ENOMEM if staging fails. */
+int su3s_field_upload(su3s_field* f, const double* host_canonical, size_t n_doubles, void* stream);
+
+/* Download to host memory: unpack into a library-owned staging buffer and
+ * copy n_doubles canonical AoS doubles to host_canonical.  The data is in
+ * place once the stream reaches this point (synchronise before reading). */
+int su3s_field_download(const su3s_field* f, double* host_canonical, size_t n_doubles,
+                        void* stream);
+
+/* ------------------------------------------------------------------------
+ * Expressions (Sec. 3, Listing 1: the expression-template tree)
+ * ---------------------------------------------------------------------- */
+
+/* Nodes are immutable and reference-counted: a node holds references to its
+ * children, so the caller may free children after building a parent.  The
+ * caller frees every handle it receives with su3s_expr_free.  Type rules:
+ * matrix*matrix -> matrix, matrix*vector -> vector, real*real -> real;
+ * add/sub need equal kinds; adj only on matrices; scale keeps the kind.
+ * ETYPE on a violation, EINVAL on null arguments.  Trees are evaluated as
+ * written (a*b*c built as mul(mul(a,b),c) is (a*b)*c, as C++ operators
+ * associate in Listing 2). */
+int su3s_expr_leaf(su3s_field* f, su3s_expr** out);
+int su3s_expr_mul(const su3s_expr* x, const su3s_expr* y, su3s_expr** out);
+int su3s_expr_add(const su3s_expr* x, const su3s_expr* y, su3s_expr** out);
+int su3s_expr_sub(const su3s_expr* x, const su3s_expr* y, su3s_expr** out);
+int su3s_expr_scale(double s, const su3s_expr* x, su3s_expr** out);
+int su3s_expr_adj(const su3s_expr* x, su3s_expr** out);
+int su3s_expr_free(su3s_expr* e);
+
+/* Canonical signature of a tree (leaves numbered by first appearance, e.g.
+ * "add(mul(M0,M1),mul(M2,M3))") copied into buf (NUL-terminated, truncated
+ * to cap bytes).  Used to see which kernel a tree maps to. */
+int su3s_expr_signature(const su3s_expr* e, char* buf, size_t cap);
+
+/* ------------------------------------------------------------------------
+ * Evaluation: dest = expr at every site, in one read/write sweep
+ * (Sec. 3, Listing 1: for(ss) _odata[ss] = eval(ss, expr);
+ *  Sec. 4, Listing 3: z = x*y)
+ * ---------------------------------------------------------------------- */
+
+/* Evaluate `e` into `dest` on `stream` with the default arithmetic.  Every
+ * leaf and dest must share lattice geometry, nmu, layout (and block) and
+ * precision; dest's kind must equal the tree's kind.  dest may be one of the
+ * leaves: every site object is read in full before it is written.  Trees in
+ * the compiled catalogue run a specialised fused kernel; others run a
+ * uniform per-site interpreter kernel (still one pass).  Reduced precisions
+ * (FP32/BF16/FP16, FP32 accumulation) and the C12 formats support the
+ * catalogue trees listed by su3s_catalogue; others return EUNSUPPORTED.
+ * C12 destinations accept only products of special unitary matrices. */
+int su3s_eval(su3s_field* dest, const su3s_expr* e, void* stream);
+
+/* As su3s_eval with an explicit arithmetic for FP64 storage:
+ *   SU3S_MATH_F64   IEEE FP64 with FMA (the GB300's FP64 pipe is narrow, so
+ *                   this path is bound by FP64 throughput, not memory);
+ *   SU3S_MATH_DF32  each FP64 input is split exactly-enough into a pair of
+ *                   FP32 values (integer bit operations, no FP64 instruction),
+ *                   products and sums use error-free transformations in FP32,
+ *                   and results are re-assembled into FP64 bit patterns.
+ *                   Error per output <= ~2^-46 * sum_t |x_t y_t| (+ 2^-52 |z|);
+ *                   needs every |input| and |intermediate| < 2^126, and values
+ *                   below 2^-126 in magnitude may be flushed to zero.
+ * Ignored for reduced-precision storage. */
+int su3s_eval_math(su3s_field* dest, const su3s_expr* e, int math, void* stream);
+
+/* Set the arithmetic SU3S_MATH_DEFAULT stands for (process-wide; initially
+ * SU3S_MATH_DF32).  EINVAL for other values. */
+int su3s_set_default_math(int math);
+
+/* Names of the compiled catalogue trees, one per line, into buf (truncated to
+ * cap bytes, NUL-terminated). */
+int su3s_catalogue(char* buf, size_t cap);
+
+/* Fix the launch geometry used for `e` into `dest` (threads per block
+ * 32..1024, multiple of 32; blocks_per_sm 0 = one thread per site-vector,
+ * else a grid-stride grid of blocks_per_sm * SMs blocks).  Results do not
+ * depend on the geometry.  Applies to later su3s_eval calls with the same
+ * kernel and volume. */
+int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int threads,
+                    int blocks_per_sm);
+
+/* Autotune the launch geometry for `e` into `dest`: times each candidate
+ * (threads 64..512, full or grid-stride grids) with CUDA events on `stream`
+ * (synchronising it; dest is overwritten), keeps the fastest for later
+ * su3s_eval calls and reports it in *threads / *blocks_per_sm (either may be
+ * NULL) and its time in *best_ms (may be NULL). */
+int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream, int* threads,
+              int* blocks_per_sm, float* best_ms);
+
+/* ------------------------------------------------------------------------
+ * Batching: many (dest, expr) pairs of uneven volumes in one persistent
+ * launch, captured in a CUDA graph
+ * ---------------------------------------------------------------------- */
+
+int su3s_batch_create(su3s_batch** out);
+/* Queue dest = e.  The batch keeps references to the expression; fields must
+ * outlive the batch.  Items must use FP64 storage. */
+int su3s_batch_add(su3s_batch* b, su3s_field* dest, const su3s_expr* e);
+/* Freeze the batch: build the tile list (tile_sites sites per tile; 0 = the
+ * library's choice) and item table in library-owned device memory, choose
+ * the persistent grid (threads per block; 0 = default) and capture the
+ * launch into a CUDA graph on `stream`.  Items whose tree the persistent
+ * kernel does not cover are captured as separate launches in the same graph.
+ * math as for su3s_eval_math. */
+int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_sites, void* stream);
+/* Replay the graph on `stream`. */
+int su3s_batch_launch(su3s_batch* b, void* stream);
+/* Sites in the batch (sum of padded volumes times links) in *sites and the
+ * number of tiles in *tiles (either may be NULL). */
+int su3s_batch_info(const su3s_batch* b, int64_t* sites, int64_t* tiles);
+int su3s_batch_destroy(su3s_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Differentiation
+ * ---------------------------------------------------------------------- */
+
+/* Reverse mode through `e` for a real loss L whose gradient with respect to
+ * the tree's value is the field `grad_out` (same shape as the tree's value;
+ * gradient convention dL/dRe + i dL/dIm).  Writes dL/d(leaf) for the unique
+ * leaves of `e` in order of first appearance into grad_leaves[k]
+ * (overwritten, not accumulated; NULL entries are skipped).  nleaves must
+ * equal the number of unique leaves.  For z = a*b this is dA = G B^dagger,
+ * dB = A^dagger G; sums, scalings and adjoints follow the chain rule.
+ * One pass: every leaf and grad_out is read once, every gradient written
+ * once.  FP64 storage only; catalogue trees only (EUNSUPPORTED otherwise). */
+int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* grad_out, su3s_field* const* grad_leaves,
+                      int nleaves, int math, void* stream);
+
+/* Number of unique leaves of `e` in *n. */
+int su3s_expr_num_leaves(const su3s_expr* e, int* n);
+
+/* ------------------------------------------------------------------------
+ * Reductions and projections
+ * ---------------------------------------------------------------------- */
+
+/* *dev_out (device memory, one double) = sum over sites, links and
+ * components of x*y over all reals = sum_x Re tr(X^dagger Y) for matrix
+ * fields.  FP64 storage, same shape.  Deterministic (fixed reduction order);
+ * uses library-allocated stream-ordered scratch for block partial sums. */
+int su3s_field_redot(const su3s_field* x, const su3s_field* y, double* dev_out, void* stream);
+
+/* dst = projection of src to SU(3) at every site object: Gram-Schmidt over
+ * rows (two sweeps) and division by the principal cube root of the
+ * determinant's phase, in native FP64 after widening the stored values; the
+ * result is rounded to dst's precision on store.  Matrix fields of equal
+ * shape and precision (FP64, FP32, BF16 or FP16; two-row storage is special
+ * unitary by construction and returns EUNSUPPORTED).  dst may equal src.
+ * Pad sites are not touched. */
+int su3s_reunitarize(su3s_field* dst, const su3s_field* src, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SU3S_H */

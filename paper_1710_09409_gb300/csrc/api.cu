@@ -1,0 +1,737 @@
+// C ABI of the su3s library: lattices, fields, expression trees, evaluation
+// planning and dispatch, upload/download, tuning, adjoint.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "dev_kernels.cuh"
+#include "internal.h"
+
+using namespace su3s;
+
+namespace su3s {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SU3S_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static int ok() {
+  g_err.clear();
+  return SU3S_OK;
+}
+
+// ---------------------------------------------------------------- registry
+static std::mutex g_reg_mu;
+static std::map<std::tuple<std::string, int, int>, EvalEntry>& eval_reg() {
+  static std::map<std::tuple<std::string, int, int>, EvalEntry> m;
+  return m;
+}
+static std::map<std::pair<std::string, int>, EvalEntry>& adj_reg() {
+  static std::map<std::pair<std::string, int>, EvalEntry> m;
+  return m;
+}
+
+void register_eval(const std::string& sig, int prec, int math, LaunchFn fn, const void* kernel,
+                   int vps) {
+  eval_reg()[std::make_tuple(sig, prec, math)] = EvalEntry{fn, kernel, vps};
+}
+
+void register_adjoint(const std::string& sig, int math, LaunchFn fn, const void* kernel) {
+  adj_reg()[std::make_pair(sig, math)] = EvalEntry{fn, kernel, 1};
+}
+
+void ensure_registered() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    register_cat_f64();
+    register_cat_df();
+    register_cat_df2();
+    register_cat_lp();
+    register_adj_f64();
+    register_adj_df();
+  });
+}
+
+const EvalEntry* find_eval(const std::string& sig, int prec, int math) {
+  ensure_registered();
+  auto it = eval_reg().find(std::make_tuple(sig, prec, math));
+  return it == eval_reg().end() ? nullptr : &it->second;
+}
+
+const EvalEntry* find_adjoint(const std::string& sig, int math) {
+  ensure_registered();
+  auto it = adj_reg().find(std::make_pair(sig, math));
+  return it == adj_reg().end() ? nullptr : &it->second;
+}
+
+// --------------------------------------------------------------- geometry
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+struct Geo {
+  int threads, bps;
+};
+static std::mutex g_geo_mu;
+static std::map<std::tuple<const void*, int64_t, int>, Geo> g_geo;
+
+void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int bps) {
+  std::lock_guard<std::mutex> lk(g_geo_mu);
+  g_geo[std::make_tuple(kernel, nvec, nmu)] = Geo{threads, bps};
+}
+
+void launch_geometry(const void* kernel, int64_t nvec, int nmu, dim3* grid, dim3* block) {
+  Geo g{256, 0};
+  {
+    std::lock_guard<std::mutex> lk(g_geo_mu);
+    auto it = g_geo.find(std::make_tuple(kernel, nvec, nmu));
+    if (it != g_geo.end()) g = it->second;
+  }
+  int64_t nb;
+  if (g.bps > 0) {
+    nb = (int64_t)g.bps * sm_count();
+    int64_t need = (nvec + g.threads - 1) / g.threads;
+    if (nb > need) nb = need;
+  } else {
+    nb = (nvec + g.threads - 1) / g.threads;
+  }
+  if (nb < 1) nb = 1;
+  if (nb > 0x7FFFFFFF) nb = 0x7FFFFFFF;
+  *grid = dim3((unsigned)nb, (unsigned)nmu, 1);
+  *block = dim3((unsigned)g.threads, 1, 1);
+}
+
+// ------------------------------------------------------------- mem pool
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  static cudaMemPool_t pool = nullptr;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pool) {
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) {
+        pool = nullptr;
+        return e;
+      }
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+cudaError_t scratch_free(void* p, cudaStream_t st) { return cudaFreeAsync(p, st); }
+
+// ------------------------------------------------------------ field shape
+int check_same_shape(const su3s_field* a, const su3s_field* b, bool same_prec) {
+  for (int d = 0; d < 4; ++d)
+    if (a->L[d] != b->L[d]) return fail(SU3S_ESHAPE, "fields live on different lattices");
+  if (a->nmu != b->nmu) return fail(SU3S_ESHAPE, "fields have different link counts");
+  if (a->layout != b->layout || (a->layout == SU3S_AOSOA && a->block != b->block))
+    return fail(SU3S_ESHAPE, "fields have different device layouts");
+  if (same_prec && a->prec != b->prec)
+    return fail(SU3S_ESHAPE, "fields have different storage precisions");
+  return SU3S_OK;
+}
+
+static int ncomp_of(int kind, int prec) {
+  if (kind == SU3S_MATRIX) return (prec == SU3S_F64_C12 || prec == SU3S_F32_C12) ? 6 : 9;
+  if (kind == SU3S_VECTOR) return 3;
+  return 1;
+}
+
+static int elem_bytes_of(int kind, int prec) {
+  if (kind == SU3S_REAL) return 8;
+  switch (prec) {
+    case SU3S_F64:
+    case SU3S_F64_C12: return 16;
+    case SU3S_F32:
+    case SU3S_F32_C12: return 8;
+    default: return 4;
+  }
+}
+
+static int layout_check(const su3s_lattice* lat, int kind, int nmu, int prec, int layout,
+                        int block) {
+  if (!lat) return fail(SU3S_EINVAL, "null lattice");
+  if (kind < SU3S_MATRIX || kind > SU3S_REAL) return fail(SU3S_EINVAL, "bad field kind %d", kind);
+  if (nmu < 1 || nmu > 8) return fail(SU3S_EINVAL, "links per site must be 1..8, got %d", nmu);
+  if (prec < SU3S_F64 || prec > SU3S_F32_C12) return fail(SU3S_EINVAL, "bad precision %d", prec);
+  if (layout != SU3S_SOA && layout != SU3S_AOSOA) return fail(SU3S_EINVAL, "bad layout %d", layout);
+  if (layout == SU3S_AOSOA && (block < 4 || block > 1024 || (block & (block - 1))))
+    return fail(SU3S_EINVAL, "site block must be a power of two in 4..1024, got %d", block);
+  if (kind == SU3S_REAL && prec != SU3S_F64)
+    return fail(SU3S_EUNSUPPORTED, "real fields are stored in FP64 only");
+  if (kind != SU3S_MATRIX && (prec == SU3S_F64_C12 || prec == SU3S_F32_C12))
+    return fail(SU3S_EUNSUPPORTED, "two-row storage exists for matrices only");
+  return SU3S_OK;
+}
+
+static int64_t vpad_of(int64_t V, int layout, int block) {
+  int64_t q = layout == SU3S_SOA ? 64 : (block < 4 ? 4 : block);
+  return (V + q - 1) / q * q;
+}
+
+static void fill_desc(su3s_field* f) {
+  FieldDesc& d = f->desc;
+  d.ptr = f->ptr;
+  const int64_t nc = f->ncomp;
+  if (f->layout == SU3S_SOA) {
+    d.logB = 31;
+    d.mask = 0x7FFFFFFFu;
+    d.s_c = f->Vpad;
+    d.s_mu = nc * f->Vpad;
+    d.s_blk = 0;
+  } else {
+    int lb = 0;
+    while ((1 << lb) < f->block) ++lb;
+    d.logB = lb;
+    d.mask = (uint32_t)(f->block - 1);
+    d.s_c = f->block;
+    d.s_mu = nc * f->block;
+    d.s_blk = (int64_t)f->nmu * nc * f->block;
+  }
+}
+
+// ------------------------------------------------------------- canonical
+static int canon_rec(const su3s_expr* e, Canon* c) {
+  switch (e->op) {
+    case 0: {
+      int slot = -1;
+      for (size_t i = 0; i < c->leaves.size(); ++i)
+        if (c->leaves[i] == e->f) slot = (int)i;
+      if (slot < 0) {
+        slot = (int)c->leaves.size();
+        c->leaves.push_back(e->f);
+      }
+      const char* k = e->kind == SU3S_MATRIX ? "M" : e->kind == SU3S_VECTOR ? "V" : "R";
+      c->sig += k + std::to_string(slot);
+      return SU3S_OK;
+    }
+    case 1:
+    case 2:
+    case 3: {
+      c->sig += e->op == 1 ? "mul(" : e->op == 2 ? "add(" : "sub(";
+      int rc = canon_rec(e->a, c);
+      if (rc) return rc;
+      c->sig += ",";
+      rc = canon_rec(e->b, c);
+      if (rc) return rc;
+      c->sig += ")";
+      return SU3S_OK;
+    }
+    case 4: {
+      int k = (int)c->scalars.size();
+      c->scalars.push_back(e->s);
+      c->sig += "scale(s" + std::to_string(k) + ",";
+      int rc = canon_rec(e->a, c);
+      if (rc) return rc;
+      c->sig += ")";
+      return SU3S_OK;
+    }
+    case 5: {
+      c->sig += "adj(";
+      int rc = canon_rec(e->a, c);
+      if (rc) return rc;
+      c->sig += ")";
+      return SU3S_OK;
+    }
+  }
+  return fail(SU3S_EINVAL, "corrupt expression node");
+}
+
+int canonicalize(const su3s_expr* e, Canon* out) {
+  out->sig.clear();
+  out->leaves.clear();
+  out->scalars.clear();
+  int rc = canon_rec(e, out);
+  if (rc) return rc;
+  out->kind = e->kind;
+  if ((int)out->leaves.size() > kMaxLeaves)
+    return fail(SU3S_EUNSUPPORTED, "expression has %zu distinct fields; at most %d",
+                out->leaves.size(), kMaxLeaves);
+  if ((int)out->scalars.size() > kMaxScalars)
+    return fail(SU3S_EUNSUPPORTED, "expression has %zu real factors; at most %d",
+                out->scalars.size(), kMaxScalars);
+  return SU3S_OK;
+}
+
+static int g_default_math = SU3S_MATH_DF32;
+
+// Internal arithmetic id for a storage precision and a requested SU3S_MATH_*.
+int resolve_math(int prec, int math) {
+  if (prec == SU3S_F64 || prec == SU3S_F64_C12) {
+    int m = math == SU3S_MATH_DEFAULT ? g_default_math : math;
+    return m == SU3S_MATH_F64 ? MATH_F64 : MATH_DF;
+  }
+  return MATH_F32;
+}
+
+static int math_for(int prec, int math) { return resolve_math(prec, math); }
+
+static void split_scalar(double s, float* h, float* l) {
+  float hh = (float)s;
+  *h = hh;
+  *l = (float)(s - (double)hh);
+}
+
+int build_params(const Canon& c, const su3s_field* dest, int vps, KParams* p) {
+  memset(p, 0, sizeof *p);
+  for (size_t i = 0; i < c.leaves.size(); ++i) p->leaf[i] = c.leaves[i]->desc;
+  p->dst = dest->desc;
+  for (size_t k = 0; k < c.scalars.size(); ++k) {
+    p->sc[k] = c.scalars[k];
+    split_scalar(c.scalars[k], &p->sch[k], &p->scl[k]);
+  }
+  p->nvec = dest->Vpad / vps;
+  p->nmu = dest->nmu;
+  return SU3S_OK;
+}
+
+// Trees made of products and adjoints of matrices only (closed in SU(3)).
+static bool su3_closed(const su3s_expr* e) {
+  if (e->op == 0) return e->kind == SU3S_MATRIX;
+  if (e->op == 1) return su3_closed(e->a) && su3_closed(e->b);
+  if (e->op == 5) return su3_closed(e->a);
+  return false;
+}
+
+static int check_eval(su3s_field* dest, const su3s_expr* e, Canon* c) {
+  if (!dest || !e) return fail(SU3S_EINVAL, "null destination or expression");
+  int rc = canonicalize(e, c);
+  if (rc) return rc;
+  if (c->kind != dest->kind)
+    return fail(SU3S_ETYPE, "destination kind %d differs from the expression's kind %d",
+                dest->kind, c->kind);
+  for (su3s_field* f : c->leaves) {
+    rc = check_same_shape(f, dest, true);
+    if (rc) return rc;
+  }
+  if ((dest->prec == SU3S_F64_C12 || dest->prec == SU3S_F32_C12) && !su3_closed(e))
+    return fail(SU3S_EUNSUPPORTED,
+                "two-row storage holds SU(3) matrices: only products and adjoints of "
+                "matrices can be stored in it");
+  return SU3S_OK;
+}
+
+static int do_eval(su3s_field* dest, const su3s_expr* e, int math, cudaStream_t st) {
+  Canon c;
+  int rc = check_eval(dest, e, &c);
+  if (rc) return rc;
+  const int m = math_for(dest->prec, math);
+  const EvalEntry* ent = find_eval(c.sig, dest->prec, m);
+  if (!ent) {
+    if (dest->prec == SU3S_F64) return interp_eval(e, c, dest, m, st);
+    return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s in storage precision %d",
+                c.sig.c_str(), dest->prec);
+  }
+  KParams p;
+  build_params(c, dest, ent->vps, &p);
+  dim3 grid, block;
+  launch_geometry(ent->kernel, p.nvec, p.nmu, &grid, &block);
+  cudaError_t ce = ent->launch(&p, grid, block, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "evaluation kernel launch");
+  return ok();
+}
+
+}  // namespace su3s
+
+// =================================================================== C ABI
+SU3S_EXPORT const char* su3s_last_error(void) { return g_err.c_str(); }
+
+SU3S_EXPORT int su3s_version(void) { return 10000; }
+
+SU3S_EXPORT int su3s_lattice_create(int lx, int ly, int lz, int lt, su3s_lattice** out) {
+  if (!out) return fail(SU3S_EINVAL, "null output handle");
+  *out = nullptr;
+  if (lx < 1 || ly < 1 || lz < 1 || lt < 1)
+    return fail(SU3S_EINVAL, "lattice extents must be >= 1 (got %d %d %d %d)", lx, ly, lz, lt);
+  int64_t v = (int64_t)lx * ly * lz * lt;
+  if (v >= (int64_t)1 << 31) return fail(SU3S_EINVAL, "lattice volume %lld >= 2^31", (long long)v);
+  su3s_lattice* l = new (std::nothrow) su3s_lattice;
+  if (!l) return fail(SU3S_ENOMEM, "out of host memory");
+  l->L[0] = lx;
+  l->L[1] = ly;
+  l->L[2] = lz;
+  l->L[3] = lt;
+  l->V = v;
+  *out = l;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_lattice_destroy(su3s_lattice* lat) {
+  delete lat;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_lattice_volume(const su3s_lattice* lat, int64_t* out) {
+  if (!lat || !out) return fail(SU3S_EINVAL, "null argument");
+  *out = lat->V;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_bytes(const su3s_lattice* lat, int kind, int nmu, int prec, int layout,
+                                 int block, size_t* bytes) {
+  if (!bytes) return fail(SU3S_EINVAL, "null output");
+  int rc = layout_check(lat, kind, nmu, prec, layout, block);
+  if (rc) return rc;
+  int64_t vp = vpad_of(lat->V, layout, block);
+  *bytes = (size_t)vp * nmu * ncomp_of(kind, prec) * elem_bytes_of(kind, prec);
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_wrap(const su3s_lattice* lat, int kind, int nmu, int prec, int layout,
+                                int block, void* dev_ptr, size_t bytes, su3s_field** out) {
+  if (!out) return fail(SU3S_EINVAL, "null output handle");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = su3s_field_bytes(lat, kind, nmu, prec, layout, block, &need);
+  if (rc) return rc;
+  if (!dev_ptr) return fail(SU3S_EINVAL, "null device pointer");
+  if (((uintptr_t)dev_ptr) & 15) return fail(SU3S_EINVAL, "device pointer is not 16-byte aligned");
+  if (bytes < need)
+    return fail(SU3S_ESHAPE, "buffer of %zu bytes is smaller than the %zu the field needs", bytes,
+                need);
+  su3s_field* f = new (std::nothrow) su3s_field;
+  if (!f) return fail(SU3S_ENOMEM, "out of host memory");
+  memcpy(f->L, lat->L, sizeof f->L);
+  f->V = lat->V;
+  f->Vpad = vpad_of(lat->V, layout, block);
+  f->kind = kind;
+  f->nmu = nmu;
+  f->prec = prec;
+  f->layout = layout;
+  f->block = layout == SU3S_AOSOA ? block : 0;
+  f->ncomp = ncomp_of(kind, prec);
+  f->elem_bytes = elem_bytes_of(kind, prec);
+  f->ptr = dev_ptr;
+  f->bytes = bytes;
+  fill_desc(f);
+  *out = f;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_destroy(su3s_field* f) {
+  delete f;
+  return ok();
+}
+
+static size_t canon_doubles(const su3s_field* f) {
+  int w = f->kind == SU3S_MATRIX ? 18 : f->kind == SU3S_VECTOR ? 6 : 1;
+  return (size_t)f->V * f->nmu * w;
+}
+
+SU3S_EXPORT int su3s_field_pack(su3s_field* f, const double* dev_canonical, void* stream) {
+  if (!f || !dev_canonical) return fail(SU3S_EINVAL, "null argument");
+  cudaError_t e = launch_pack(f, dev_canonical, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pack kernel");
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_unpack(const su3s_field* f, double* dev_canonical, void* stream) {
+  if (!f || !dev_canonical) return fail(SU3S_EINVAL, "null argument");
+  cudaError_t e = launch_unpack(f, dev_canonical, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "unpack kernel");
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_upload(su3s_field* f, const double* host, size_t n, void* stream) {
+  if (!f || !host) return fail(SU3S_EINVAL, "null argument");
+  if (n != canon_doubles(f))
+    return fail(SU3S_ESHAPE, "host array has %zu doubles, the field needs %zu", n, canon_doubles(f));
+  cudaStream_t st = (cudaStream_t)stream;
+  void* stage = nullptr;
+  cudaError_t e = scratch_alloc(&stage, n * sizeof(double), st);
+  if (e != cudaSuccess) return fail(SU3S_ENOMEM, "staging allocation of %zu bytes failed: %s",
+                                    n * sizeof(double), cudaGetErrorString(e));
+  e = cudaMemcpyAsync(stage, host, n * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_pack(f, (const double*)stage, st);
+  cudaError_t e2 = scratch_free(stage, st);
+  if (e != cudaSuccess) return cuda_fail(e, "upload");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "upload staging release");
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_download(const su3s_field* f, double* host, size_t n, void* stream) {
+  if (!f || !host) return fail(SU3S_EINVAL, "null argument");
+  if (n != canon_doubles(f))
+    return fail(SU3S_ESHAPE, "host array has %zu doubles, the field holds %zu", n, canon_doubles(f));
+  cudaStream_t st = (cudaStream_t)stream;
+  void* stage = nullptr;
+  cudaError_t e = scratch_alloc(&stage, n * sizeof(double), st);
+  if (e != cudaSuccess) return fail(SU3S_ENOMEM, "staging allocation of %zu bytes failed: %s",
+                                    n * sizeof(double), cudaGetErrorString(e));
+  e = launch_unpack(f, (double*)stage, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, stage, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaError_t e2 = scratch_free(stage, st);
+  if (e != cudaSuccess) return cuda_fail(e, "download");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "download staging release");
+  return ok();
+}
+
+// ----------------------------------------------------------- expressions
+static int new_node(int op, int kind, const su3s_expr* a, const su3s_expr* b, su3s_field* f,
+                    double s, su3s_expr** out) {
+  su3s_expr* e = new (std::nothrow) su3s_expr;
+  if (!e) return fail(SU3S_ENOMEM, "out of host memory");
+  e->op = op;
+  e->kind = kind;
+  e->a = a;
+  e->b = b;
+  e->f = f;
+  e->s = s;
+  if (a) const_cast<su3s_expr*>(a)->ref.fetch_add(1);
+  if (b) const_cast<su3s_expr*>(b)->ref.fetch_add(1);
+  *out = e;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_expr_leaf(su3s_field* f, su3s_expr** out) {
+  if (!f || !out) return fail(SU3S_EINVAL, "null argument");
+  return new_node(0, f->kind, nullptr, nullptr, f, 0.0, out);
+}
+
+SU3S_EXPORT int su3s_expr_mul(const su3s_expr* x, const su3s_expr* y, su3s_expr** out) {
+  if (!x || !y || !out) return fail(SU3S_EINVAL, "null argument");
+  int k;
+  if (x->kind == SU3S_MATRIX && y->kind == SU3S_MATRIX) k = SU3S_MATRIX;
+  else if (x->kind == SU3S_MATRIX && y->kind == SU3S_VECTOR) k = SU3S_VECTOR;
+  else if (x->kind == SU3S_REAL && y->kind == SU3S_REAL) k = SU3S_REAL;
+  else return fail(SU3S_ETYPE, "product of kinds %d and %d is not defined", x->kind, y->kind);
+  return new_node(1, k, x, y, nullptr, 0.0, out);
+}
+
+SU3S_EXPORT int su3s_expr_add(const su3s_expr* x, const su3s_expr* y, su3s_expr** out) {
+  if (!x || !y || !out) return fail(SU3S_EINVAL, "null argument");
+  if (x->kind != y->kind) return fail(SU3S_ETYPE, "sum of different kinds");
+  return new_node(2, x->kind, x, y, nullptr, 0.0, out);
+}
+
+SU3S_EXPORT int su3s_expr_sub(const su3s_expr* x, const su3s_expr* y, su3s_expr** out) {
+  if (!x || !y || !out) return fail(SU3S_EINVAL, "null argument");
+  if (x->kind != y->kind) return fail(SU3S_ETYPE, "difference of different kinds");
+  return new_node(3, x->kind, x, y, nullptr, 0.0, out);
+}
+
+SU3S_EXPORT int su3s_expr_scale(double s, const su3s_expr* x, su3s_expr** out) {
+  if (!x || !out) return fail(SU3S_EINVAL, "null argument");
+  return new_node(4, x->kind, x, nullptr, nullptr, s, out);
+}
+
+SU3S_EXPORT int su3s_expr_adj(const su3s_expr* x, su3s_expr** out) {
+  if (!x || !out) return fail(SU3S_EINVAL, "null argument");
+  if (x->kind != SU3S_MATRIX) return fail(SU3S_ETYPE, "adjoint of a non-matrix");
+  return new_node(5, SU3S_MATRIX, x, nullptr, nullptr, 0.0, out);
+}
+
+SU3S_EXPORT int su3s_expr_free(su3s_expr* e) {
+  // iterative release of a reference-counted DAG
+  std::vector<const su3s_expr*> todo;
+  if (e) todo.push_back(e);
+  while (!todo.empty()) {
+    su3s_expr* n = const_cast<su3s_expr*>(todo.back());
+    todo.pop_back();
+    if (n->ref.fetch_sub(1) == 1) {
+      if (n->a) todo.push_back(n->a);
+      if (n->b) todo.push_back(n->b);
+      delete n;
+    }
+  }
+  return ok();
+}
+
+SU3S_EXPORT int su3s_expr_signature(const su3s_expr* e, char* buf, size_t cap) {
+  if (!e || !buf || cap == 0) return fail(SU3S_EINVAL, "null argument");
+  Canon c;
+  int rc = canonicalize(e, &c);
+  if (rc && rc != SU3S_EUNSUPPORTED) return rc;
+  snprintf(buf, cap, "%s", c.sig.c_str());
+  return ok();
+}
+
+SU3S_EXPORT int su3s_expr_num_leaves(const su3s_expr* e, int* n) {
+  if (!e || !n) return fail(SU3S_EINVAL, "null argument");
+  Canon c;
+  int rc = canonicalize(e, &c);
+  if (rc) return rc;
+  *n = (int)c.leaves.size();
+  return ok();
+}
+
+// ------------------------------------------------------------- evaluation
+SU3S_EXPORT int su3s_eval(su3s_field* dest, const su3s_expr* e, void* stream) {
+  return do_eval(dest, e, SU3S_MATH_DEFAULT, (cudaStream_t)stream);
+}
+
+SU3S_EXPORT int su3s_eval_math(su3s_field* dest, const su3s_expr* e, int math, void* stream) {
+  if (math != SU3S_MATH_DEFAULT && math != SU3S_MATH_F64 && math != SU3S_MATH_DF32)
+    return fail(SU3S_EINVAL, "bad arithmetic %d", math);
+  return do_eval(dest, e, math, (cudaStream_t)stream);
+}
+
+SU3S_EXPORT int su3s_set_default_math(int math) {
+  if (math != SU3S_MATH_F64 && math != SU3S_MATH_DF32)
+    return fail(SU3S_EINVAL, "default arithmetic must be SU3S_MATH_F64 or SU3S_MATH_DF32");
+  g_default_math = math;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_catalogue(char* buf, size_t cap) {
+  if (!buf || cap == 0) return fail(SU3S_EINVAL, "null argument");
+  ensure_registered();
+  std::string out;
+  static const char* pn[] = {"f64", "f32", "bf16", "f16", "f64_c12", "f32_c12"};
+  static const char* mn[] = {"", "f64", "df32", "f32"};
+  for (auto& kv : eval_reg()) {
+    out += "eval " + std::get<0>(kv.first) + " " + pn[std::get<1>(kv.first)] + " " +
+           mn[std::get<2>(kv.first)] + "\n";
+  }
+  for (auto& kv : adj_reg()) out += "adjoint " + kv.first.first + " f64 " + mn[kv.first.second] + "\n";
+  snprintf(buf, cap, "%s", out.c_str());
+  return ok();
+}
+
+SU3S_EXPORT int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int threads,
+                                int blocks_per_sm) {
+  if (threads < 32 || threads > 256 || threads % 32)
+    return fail(SU3S_EINVAL, "threads per block must be a multiple of 32 in 32..256");
+  if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(SU3S_EINVAL, "bad blocks per SM");
+  Canon c;
+  int rc = check_eval(const_cast<su3s_field*>(dest), e, &c);
+  if (rc) return rc;
+  const EvalEntry* ent = find_eval(c.sig, dest->prec, math_for(dest->prec, math));
+  if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s", c.sig.c_str());
+  set_geometry(ent->kernel, dest->Vpad / ent->vps, dest->nmu, threads, blocks_per_sm);
+  return ok();
+}
+
+SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream,
+                          int* threads_out, int* bps_out, float* best_ms) {
+  Canon c;
+  int rc = check_eval(dest, e, &c);
+  if (rc) return rc;
+  const int m = math_for(dest->prec, math);
+  const EvalEntry* ent = find_eval(c.sig, dest->prec, m);
+  if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s", c.sig.c_str());
+  cudaStream_t st = (cudaStream_t)stream;
+  KParams p;
+  build_params(c, dest, ent->vps, &p);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(SU3S_ECUDA, "event creation failed");
+  const int th_c[] = {64, 128, 256};
+  const int bps_c[] = {0, 2, 4, 8, 16};
+  float best = 1e30f;
+  int bt = 256, bb = 0;
+  for (int th : th_c)
+    for (int bps : bps_c) {
+      set_geometry(ent->kernel, p.nvec, p.nmu, th, bps);
+      dim3 grid, block;
+      launch_geometry(ent->kernel, p.nvec, p.nmu, &grid, &block);
+      cudaError_t ce = ent->launch(&p, grid, block, st);  // warm-up
+      if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(ce, "tuning launch");
+      }
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3; ++r) ent->launch(&p, grid, block, st);
+      cudaEventRecord(e1, st);
+      ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(ce, "tuning run");
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= 3.f;
+      if (ms < best) {
+        best = ms;
+        bt = th;
+        bb = bps;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_geometry(ent->kernel, p.nvec, p.nmu, bt, bb);
+  if (threads_out) *threads_out = bt;
+  if (bps_out) *bps_out = bb;
+  if (best_ms) *best_ms = best;
+  return ok();
+}
+
+// ---------------------------------------------------------------- adjoint
+SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
+                                  su3s_field* const* gleaves, int nleaves, int math, void* stream) {
+  if (!e || !gout) return fail(SU3S_EINVAL, "null argument");
+  Canon c;
+  int rc = canonicalize(e, &c);
+  if (rc) return rc;
+  if (nleaves != (int)c.leaves.size())
+    return fail(SU3S_EINVAL, "expression has %zu distinct fields, %d gradients given",
+                c.leaves.size(), nleaves);
+  if (gout->kind != c.kind) return fail(SU3S_ETYPE, "gradient field kind differs from the tree's");
+  if (gout->prec != SU3S_F64) return fail(SU3S_EUNSUPPORTED, "adjoint needs FP64 storage");
+  for (size_t i = 0; i < c.leaves.size(); ++i) {
+    rc = check_same_shape(c.leaves[i], gout, true);
+    if (rc) return rc;
+    if (gleaves && gleaves[i]) {
+      rc = check_same_shape(gleaves[i], gout, true);
+      if (rc) return rc;
+      if (gleaves[i]->kind != c.leaves[i]->kind)
+        return fail(SU3S_ETYPE, "gradient %zu has the wrong kind", i);
+    }
+  }
+  if (math != SU3S_MATH_DEFAULT && math != SU3S_MATH_F64 && math != SU3S_MATH_DF32)
+    return fail(SU3S_EINVAL, "bad arithmetic %d", math);
+  const int m = math_for(SU3S_F64, math);
+  const EvalEntry* ent = find_adjoint(c.sig, m);
+  if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled adjoint kernel for %s", c.sig.c_str());
+  GParams p;
+  memset(&p, 0, sizeof p);
+  build_params(c, gout, 1, &p.k);
+  p.gout = gout->desc;
+  for (size_t i = 0; i < c.leaves.size(); ++i)
+    if (gleaves && gleaves[i]) p.gleaf[i] = gleaves[i]->desc;
+  dim3 grid, block;
+  launch_geometry(ent->kernel, p.k.nvec, p.k.nmu, &grid, &block);
+  cudaError_t ce = ent->launch(&p, grid, block, (cudaStream_t)stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "adjoint kernel launch");
+  return ok();
+}

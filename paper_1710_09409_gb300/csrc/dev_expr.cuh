@@ -1,0 +1,513 @@
+// Compile-time expression trees evaluated per site in registers.
+//
+// The tree of an expression is a type, as in the expression-template engine
+// of arXiv:1710.09409 (Sec. 3, Listing 1: LatticeBinaryExpression<Op,T1,T2>
+// and eval(ss, expr)), but here a fixed catalogue of tree types is compiled
+// ahead of time and a runtime tree is matched to one of them by its
+// signature; leaf fields and real factors are runtime values.
+//
+//   LM<i>, LV<i>, LR<i>   leaf slot i holding a matrix / vector / real field
+//   Mul<X,Y>              product (matrix*matrix, matrix*vector, real*real)
+//   Add<X,Y>, Sub<X,Y>    sum, difference
+//   Scale<k,X>            real factor number k times X
+//   Adj<X>                Hermitian adjoint of a matrix
+//
+// Forward evaluation accumulates: the terms of sums and products of a node
+// go straight into one accumulator per output real (so a*b + c*d is one
+// 12-term dot product per output real, with no intermediate rounding), and an
+// adjoint operand of a product is read transposed and conjugated in place.
+// Reverse mode (Back) applies dA = G B^dagger, dB = A^dagger G and the chain
+// rule through sums, factors and adjoints.
+#pragma once
+
+#include "dev_math.cuh"
+
+namespace su3s {
+
+enum { KM = 0, KV = 1, KR = 2 };
+
+template <int K>
+struct Width;
+template <>
+struct Width<KM> {
+  static constexpr int value = 18;
+};
+template <>
+struct Width<KV> {
+  static constexpr int value = 6;
+};
+template <>
+struct Width<KR> {
+  static constexpr int value = 1;
+};
+
+template <int I>
+struct LM {
+  static constexpr int kind = KM, slot = I, nleaf = I + 1, nsc = 0;
+  static constexpr bool is_leaf = true, accumulates = false;
+};
+template <int I>
+struct LV {
+  static constexpr int kind = KV, slot = I, nleaf = I + 1, nsc = 0;
+  static constexpr bool is_leaf = true, accumulates = false;
+};
+template <int I>
+struct LR {
+  static constexpr int kind = KR, slot = I, nleaf = I + 1, nsc = 0;
+  static constexpr bool is_leaf = true, accumulates = false;
+};
+
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+template <class X, class Y>
+struct Mul {
+  static constexpr int kind = (X::kind == KM && Y::kind == KM)   ? KM
+                              : (X::kind == KM && Y::kind == KV) ? KV
+                              : (X::kind == KR && Y::kind == KR) ? KR
+                                                                 : -1;
+  static_assert(kind >= 0, "ill-typed product");
+  static constexpr int nleaf = cmax(X::nleaf, Y::nleaf), nsc = cmax(X::nsc, Y::nsc);
+  static constexpr bool is_leaf = false, accumulates = true;
+};
+template <class X, class Y>
+struct Add {
+  static_assert(X::kind == Y::kind, "ill-typed sum");
+  static constexpr int kind = X::kind;
+  static constexpr int nleaf = cmax(X::nleaf, Y::nleaf), nsc = cmax(X::nsc, Y::nsc);
+  static constexpr bool is_leaf = false, accumulates = true;
+};
+template <class X, class Y>
+struct Sub {
+  static_assert(X::kind == Y::kind, "ill-typed difference");
+  static constexpr int kind = X::kind;
+  static constexpr int nleaf = cmax(X::nleaf, Y::nleaf), nsc = cmax(X::nsc, Y::nsc);
+  static constexpr bool is_leaf = false, accumulates = true;
+};
+template <int K, class X>
+struct Scale {
+  static constexpr int kind = X::kind;
+  static constexpr int nleaf = X::nleaf, nsc = cmax(X::nsc, K + 1);
+  static constexpr bool is_leaf = false, accumulates = true;
+};
+template <class X>
+struct Adj {
+  static_assert(X::kind == KM, "adjoint of a non-matrix");
+  static constexpr int kind = KM;
+  static constexpr int nleaf = X::nleaf, nsc = X::nsc;
+  static constexpr bool is_leaf = false, accumulates = false;
+};
+
+// Number of occurrences of leaf slot I in tree T.
+template <class T, int I>
+struct Count;
+template <int J, int I>
+struct Count<LM<J>, I> {
+  static constexpr int value = (I == J);
+};
+template <int J, int I>
+struct Count<LV<J>, I> {
+  static constexpr int value = (I == J);
+};
+template <int J, int I>
+struct Count<LR<J>, I> {
+  static constexpr int value = (I == J);
+};
+template <class X, class Y, int I>
+struct Count<Mul<X, Y>, I> {
+  static constexpr int value = Count<X, I>::value + Count<Y, I>::value;
+};
+template <class X, class Y, int I>
+struct Count<Add<X, Y>, I> {
+  static constexpr int value = Count<X, I>::value + Count<Y, I>::value;
+};
+template <class X, class Y, int I>
+struct Count<Sub<X, Y>, I> {
+  static constexpr int value = Count<X, I>::value + Count<Y, I>::value;
+};
+template <int K, class X, int I>
+struct Count<Scale<K, X>, I> {
+  static constexpr int value = Count<X, I>::value;
+};
+template <class X, int I>
+struct Count<Adj<X>, I> {
+  static constexpr int value = Count<X, I>::value;
+};
+
+// Kind of leaf slot I in tree T (-1 if absent).
+template <class T, int I>
+struct LeafKind;
+template <int J, int I>
+struct LeafKind<LM<J>, I> {
+  static constexpr int value = (I == J) ? KM : -1;
+};
+template <int J, int I>
+struct LeafKind<LV<J>, I> {
+  static constexpr int value = (I == J) ? KV : -1;
+};
+template <int J, int I>
+struct LeafKind<LR<J>, I> {
+  static constexpr int value = (I == J) ? KR : -1;
+};
+template <class X, class Y, int I>
+struct LeafKind<Mul<X, Y>, I> {
+  static constexpr int value = cmax(LeafKind<X, I>::value, LeafKind<Y, I>::value);
+};
+template <class X, class Y, int I>
+struct LeafKind<Add<X, Y>, I> {
+  static constexpr int value = cmax(LeafKind<X, I>::value, LeafKind<Y, I>::value);
+};
+template <class X, class Y, int I>
+struct LeafKind<Sub<X, Y>, I> {
+  static constexpr int value = cmax(LeafKind<X, I>::value, LeafKind<Y, I>::value);
+};
+template <int K, class X, int I>
+struct LeafKind<Scale<K, X>, I> {
+  static constexpr int value = LeafKind<X, I>::value;
+};
+template <class X, int I>
+struct LeafKind<Adj<X>, I> {
+  static constexpr int value = LeafKind<X, I>::value;
+};
+
+// Operand view: Adj<B> is read as B with the adjoint flag set.
+template <class T>
+struct Operand {
+  using base = T;
+  static constexpr bool adj = false;
+};
+template <class B>
+struct Operand<Adj<B>> {
+  using base = B;
+  static constexpr bool adj = true;
+};
+
+// Per-site evaluation context: loaded leaves and real factors.
+template <class M, int NL, int NS>
+struct Ctx {
+  typename M::R leaf[NL][18];
+  typename M::R sc[NS > 0 ? NS : 1];
+};
+
+// ----------------------------------------------------------- primitives
+// z (+)= SG * op(x) * op(y), 3x3 complex; op = adjoint when AX / AY.
+template <class M, bool FIRST, int SG, bool AX, bool AY>
+__device__ __forceinline__ void mm_acc(typename M::A* z, const typename M::R* x,
+                                       const typename M::R* y) {
+  constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      typename M::A& re = z[2 * (3 * i + k)];
+      typename M::A& im = z[2 * (3 * i + k) + 1];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int xi = AX ? (3 * j + i) : (3 * i + j);
+        const int yi = AY ? (3 * k + j) : (3 * j + k);
+        const typename M::R& xr = x[2 * xi];
+        const typename M::R& xm = x[2 * xi + 1];
+        const typename M::R& yr = y[2 * yi];
+        const typename M::R& ym = y[2 * yi + 1];
+        if (FIRST && j == 0) {
+          M::template fma<true, SG>(re, xr, yr);
+          M::template fma<true, SG * sy>(im, xr, ym);
+        } else {
+          M::template fma<false, SG>(re, xr, yr);
+          M::template fma<false, SG * sy>(im, xr, ym);
+        }
+        M::template fma<false, -SG * sx * sy>(re, xm, ym);
+        M::template fma<false, SG * sx>(im, xm, yr);
+      }
+    }
+}
+
+// z (+)= SG * op(x) * v, x 3x3, v 3-vector.
+template <class M, bool FIRST, int SG, bool AX>
+__device__ __forceinline__ void mv_acc(typename M::A* z, const typename M::R* x,
+                                       const typename M::R* v) {
+  constexpr int sx = AX ? -1 : 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    typename M::A& re = z[2 * i];
+    typename M::A& im = z[2 * i + 1];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int xi = AX ? (3 * j + i) : (3 * i + j);
+      if (FIRST && j == 0) {
+        M::template fma<true, SG>(re, x[2 * xi], v[2 * j]);
+        M::template fma<true, SG>(im, x[2 * xi], v[2 * j + 1]);
+      } else {
+        M::template fma<false, SG>(re, x[2 * xi], v[2 * j]);
+        M::template fma<false, SG>(im, x[2 * xi], v[2 * j + 1]);
+      }
+      M::template fma<false, -SG * sx>(re, x[2 * xi + 1], v[2 * j + 1]);
+      M::template fma<false, SG * sx>(im, x[2 * xi + 1], v[2 * j]);
+    }
+  }
+}
+
+// z (+)= SG * u * w^dagger (outer product of 3-vectors): z_ij = u_i conj(w_j).
+template <class M, bool FIRST, int SG>
+__device__ __forceinline__ void outer_acc(typename M::A* z, const typename M::R* u,
+                                          const typename M::R* w) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      typename M::A& re = z[2 * (3 * i + j)];
+      typename M::A& im = z[2 * (3 * i + j) + 1];
+      M::template fma<FIRST, SG>(re, u[2 * i], w[2 * j]);
+      M::template fma<false, SG>(re, u[2 * i + 1], w[2 * j + 1]);
+      M::template fma<FIRST, SG>(im, u[2 * i + 1], w[2 * j]);
+      M::template fma<false, -SG>(im, u[2 * i], w[2 * j + 1]);
+    }
+}
+
+template <class M, int W, bool FIRST, int SG>
+__device__ __forceinline__ void vec_add(typename M::A* z, const typename M::R* x) {
+#pragma unroll
+  for (int r = 0; r < W; ++r) M::template add<FIRST, SG>(z[r], x[r]);
+}
+
+template <class M, int W, bool FIRST, int SG>
+__device__ __forceinline__ void vec_scale_add(typename M::A* z, const typename M::R& s,
+                                              const typename M::R* x) {
+#pragma unroll
+  for (int r = 0; r < W; ++r) M::template fma<FIRST, SG>(z[r], s, x[r]);
+}
+
+template <class M>
+__device__ __forceinline__ void adjoint(typename M::R* z, const typename M::R* x) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      z[2 * (3 * i + j)] = x[2 * (3 * j + i)];
+      z[2 * (3 * i + j) + 1] = M::neg(x[2 * (3 * j + i) + 1]);
+    }
+}
+
+template <class M, int W>
+__device__ __forceinline__ void finish(typename M::R* z, const typename M::A* a) {
+#pragma unroll
+  for (int r = 0; r < W; ++r) z[r] = M::finish(a[r]);
+}
+
+// ------------------------------------------------------------ forward
+// Value of node T (normalised) into out[Width].
+template <class T, class M, class C>
+__device__ __forceinline__ void value(const C& ctx, typename M::R* out);
+
+// acc (+)= SG * value(T)
+template <class T, class M, bool FIRST, int SG, class C>
+__device__ __forceinline__ void acc_into(const C& ctx, typename M::A* acc);
+
+// Leaves: copy from the context.
+template <class T, class M, class C>
+__device__ __forceinline__ void value(const C& ctx, typename M::R* out) {
+  constexpr int W = Width<T::kind>::value;
+  if constexpr (T::is_leaf) {
+#pragma unroll
+    for (int r = 0; r < W; ++r) out[r] = ctx.leaf[T::slot][r];
+  } else if constexpr (T::accumulates) {
+    typename M::A a[W];
+    acc_into<T, M, true, 1>(ctx, a);
+    finish<M, W>(out, a);
+  } else {  // Adj
+    using X = typename Operand<T>::base;
+    typename M::R x[18];
+    value<X, M>(ctx, x);
+    adjoint<M>(out, x);
+  }
+}
+
+template <class M, bool FIRST, int SG, class C, class X, class Y>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Mul<X, Y>*);
+template <class M, bool FIRST, int SG, class C, class X, class Y>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Add<X, Y>*);
+template <class M, bool FIRST, int SG, class C, class X, class Y>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Sub<X, Y>*);
+template <class M, bool FIRST, int SG, class C, int K, class X>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Scale<K, X>*);
+
+template <class T, class M, bool FIRST, int SG, class C>
+__device__ __forceinline__ void acc_into(const C& ctx, typename M::A* acc) {
+  constexpr int W = Width<T::kind>::value;
+  if constexpr (!T::accumulates) {
+    typename M::R v[W];
+    value<T, M>(ctx, v);
+    vec_add<M, W, FIRST, SG>(acc, v);
+  } else {
+    acc_node<M, FIRST, SG>(ctx, acc, (T*)nullptr);
+  }
+}
+
+template <class M, bool FIRST, int SG, class C, class X, class Y>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Mul<X, Y>*) {
+  using OX = Operand<X>;
+  using OY = Operand<Y>;
+  using BX = typename OX::base;
+  using BY = typename OY::base;
+  typename M::R xv[Width<BX::kind>::value];
+  typename M::R yv[Width<BY::kind>::value];
+  value<BX, M>(ctx, xv);
+  value<BY, M>(ctx, yv);
+  if constexpr (Mul<X, Y>::kind == KM) {
+    mm_acc<M, FIRST, SG, OX::adj, OY::adj>(acc, xv, yv);
+  } else if constexpr (Mul<X, Y>::kind == KV) {
+    mv_acc<M, FIRST, SG, OX::adj>(acc, xv, yv);
+  } else {
+    M::template fma<FIRST, SG>(acc[0], xv[0], yv[0]);
+  }
+}
+
+template <class M, bool FIRST, int SG, class C, class X, class Y>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Add<X, Y>*) {
+  acc_into<X, M, FIRST, SG>(ctx, acc);
+  acc_into<Y, M, false, SG>(ctx, acc);
+}
+
+template <class M, bool FIRST, int SG, class C, class X, class Y>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Sub<X, Y>*) {
+  acc_into<X, M, FIRST, SG>(ctx, acc);
+  acc_into<Y, M, false, -SG>(ctx, acc);
+}
+
+template <class M, bool FIRST, int SG, class C, int K, class X>
+__device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Scale<K, X>*) {
+  constexpr int W = Width<X::kind>::value;
+  typename M::R v[W];
+  value<X, M>(ctx, v);
+  vec_scale_add<M, W, FIRST, SG>(acc, ctx.sc[K], v);
+}
+
+// ------------------------------------------------------------ reverse
+// Gradient accumulators of leaves that occur more than once; leaves that occur
+// once have their gradient complete when it is formed and are emitted at once
+// through the sink.
+template <class M, int NL>
+struct GradAcc {
+  typename M::A g[NL][18];
+};
+
+// gradient contribution for leaf slot I given as a ready accumulator
+template <class M, int W, int I, bool ONCE, class GA, class Sink>
+__device__ __forceinline__ void emit_acc(const typename M::A* contrib, GA& ga, Sink& sink) {
+  if constexpr (ONCE) {
+    sink.template put<I, W>(contrib);
+  } else {
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      typename M::R v = M::finish(contrib[r]);
+      M::template add<false, 1>(ga.g[I][r], v);
+    }
+  }
+}
+
+// Tree-wide occurrence counts are needed at the leaves: carry the root type.
+template <class Root>
+struct Rev {
+  template <class T, class M, class C, class GA, class Sink>
+  __device__ static __forceinline__ void run(const C& ctx, const typename M::R* G, GA& ga,
+                                             Sink& sink) {
+    constexpr int W = Width<T::kind>::value;
+    if constexpr (T::is_leaf) {
+      typename M::A a[W];
+      vec_add<M, W, true, 1>(a, G);
+      emit_acc<M, W, T::slot, Count<Root, T::slot>::value == 1>(a, ga, sink);
+    } else {
+      node<M>(ctx, G, ga, sink, (T*)nullptr);
+    }
+  }
+
+  // Feed a gradient that is a product (given as an accumulator-producing
+  // lambda) into operand node T: directly for leaves, else through a value.
+  template <class T, class M, class C, class GA, class Sink, class F>
+  __device__ static __forceinline__ void feed(const C& ctx, GA& ga, Sink& sink, F&& make) {
+    constexpr int W = Width<T::kind>::value;
+    typename M::A a[W];
+    make(a);
+    if constexpr (T::is_leaf) {
+      emit_acc<M, W, T::slot, Count<Root, T::slot>::value == 1>(a, ga, sink);
+    } else {
+      typename M::R v[W];
+      finish<M, W>(v, a);
+      run<T, M>(ctx, v, ga, sink);
+    }
+  }
+
+  template <class M, class C, class GA, class Sink, class X, class Y>
+  __device__ static __forceinline__ void node(const C& ctx, const typename M::R* G, GA& ga,
+                                              Sink& sink, Mul<X, Y>*) {
+    using OX = Operand<X>;
+    using OY = Operand<Y>;
+    using BX = typename OX::base;
+    using BY = typename OY::base;
+    constexpr bool ax = OX::adj, ay = OY::adj;
+    typename M::R xv[Width<BX::kind>::value];
+    typename M::R yv[Width<BY::kind>::value];
+    value<BX, M>(ctx, xv);
+    value<BY, M>(ctx, yv);
+    if constexpr (Mul<X, Y>::kind == KM) {
+      // d(base X): ax ? (Y G^dagger) : (G Y^dagger), with Y = op(BY)
+      feed<BX, M>(ctx, ga, sink, [&](typename M::A* a) {
+        if constexpr (ax) mm_acc<M, true, 1, ay, true>(a, yv, G);
+        else mm_acc<M, true, 1, false, !ay>(a, G, yv);
+      });
+      // d(base Y): ay ? (G^dagger X) : (X^dagger G), with X = op(BX)
+      feed<BY, M>(ctx, ga, sink, [&](typename M::A* a) {
+        if constexpr (ay) mm_acc<M, true, 1, true, ax>(a, G, xv);
+        else mm_acc<M, true, 1, !ax, false>(a, xv, G);
+      });
+    } else if constexpr (Mul<X, Y>::kind == KV) {
+      // Z = op(BX) v: d op(BX) = G v^dagger; d(BX) = ax ? v G^dagger : G v^dagger
+      feed<BX, M>(ctx, ga, sink, [&](typename M::A* a) {
+        if constexpr (ax) outer_acc<M, true, 1>(a, yv, G);
+        else outer_acc<M, true, 1>(a, G, yv);
+      });
+      // dv = op(BX)^dagger G
+      feed<BY, M>(ctx, ga, sink, [&](typename M::A* a) { mv_acc<M, true, 1, !ax>(a, xv, G); });
+    } else {
+      feed<BX, M>(ctx, ga, sink,
+                  [&](typename M::A* a) { M::template fma<true, 1>(a[0], G[0], yv[0]); });
+      feed<BY, M>(ctx, ga, sink,
+                  [&](typename M::A* a) { M::template fma<true, 1>(a[0], xv[0], G[0]); });
+    }
+  }
+
+  template <class M, class C, class GA, class Sink, class X, class Y>
+  __device__ static __forceinline__ void node(const C& ctx, const typename M::R* G, GA& ga,
+                                              Sink& sink, Add<X, Y>*) {
+    run<X, M>(ctx, G, ga, sink);
+    run<Y, M>(ctx, G, ga, sink);
+  }
+
+  template <class M, class C, class GA, class Sink, class X, class Y>
+  __device__ static __forceinline__ void node(const C& ctx, const typename M::R* G, GA& ga,
+                                              Sink& sink, Sub<X, Y>*) {
+    constexpr int W = Width<X::kind>::value;
+    run<X, M>(ctx, G, ga, sink);
+    typename M::R ng[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) ng[r] = M::neg(G[r]);
+    run<Y, M>(ctx, ng, ga, sink);
+  }
+
+  template <class M, class C, class GA, class Sink, int K, class X>
+  __device__ static __forceinline__ void node(const C& ctx, const typename M::R* G, GA& ga,
+                                              Sink& sink, Scale<K, X>*) {
+    constexpr int W = Width<X::kind>::value;
+    feed<X, M>(ctx, ga, sink,
+               [&](typename M::A* a) { vec_scale_add<M, W, true, 1>(a, ctx.sc[K], G); });
+  }
+
+  template <class M, class C, class GA, class Sink, class X>
+  __device__ static __forceinline__ void node(const C& ctx, const typename M::R* G, GA& ga,
+                                              Sink& sink, Adj<X>*) {
+    typename M::R g[18];
+    adjoint<M>(g, G);
+    run<X, M>(ctx, g, ga, sink);
+  }
+};
+
+}  // namespace su3s

@@ -1,0 +1,194 @@
+// Arithmetic policies for site-local complex 3x3 algebra on sm_103a.
+//
+//   MathF64  native IEEE FP64 with fused multiply-add.  On the GB300 the FP64
+//            pipe retires about two DFMA per clock per SM, so a 3x3 complex
+//            product (108 DFMA) caps near 5 G sites/s, far below HBM speed.
+//   MathDF   FP64-accurate arithmetic from FP32 and integer instructions only
+//            (no FP64 instruction, not even a conversion, all of which run on
+//            the narrow FP64 pipe):
+//              * an FP64 input x is split by bit operations into a pair of
+//                FP32 values xh + xl with |x - xh - xl| <= 2^-48 |x|
+//                (xh = x truncated to 24 significant bits, xl = the remaining
+//                29 bits rounded to 24 by an integer-to-float conversion);
+//              * a sum of products sum_t x_t*y_t keeps a running FP32 sum S of
+//                the leading products xh*yh and an FP32 tail `lo`; each new
+//                leading product enters S through Knuth's TwoSum, whose error
+//                term is taken with an FMA against the exact product so the
+//                product's own rounding error folds in; the cross terms
+//                xh*yl + xl*yh go into the tail by FMA (Dekker/Knuth
+//                error-free transformations, Ogita-Rump-Oishi style dot
+//                product);
+//              * the result S + lo is rounded toward zero into one FP32 value
+//                plus a same-signed remainder, and the FP64 bit pattern is
+//                assembled with integer operations: the leading value gives
+//                sign, exponent and the top 23 fraction bits, the remainder
+//                scaled to units of the last place gives the low 29 bits.
+//            Error per output ~2^-46 * sum_t |x_t y_t| + 2^-52 |z|.  Needs all
+//            magnitudes below 2^126; magnitudes below 2^-126 may be flushed.
+//   MathF32  FP32 arithmetic for FP32/BF16/FP16 storage (FP32 accumulation).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace su3s {
+
+// ----------------------------------------------------------------- helpers
+struct df {
+  float h, l;
+};
+
+// FP64 bit pattern (lo32, hi32) -> (xh, xl).  No FP64 instruction.
+__device__ __forceinline__ df df_split_bits(uint32_t lo32, uint32_t hi32) {
+  uint32_t u = hi32 & 0x7FFFFFFFu;
+  u = max(u, 0x38000000u);                   // exponents below 2^-126 collapse to 0
+  uint32_t w = u - 0x38000000u;              // rebias 1023 -> 127
+  uint32_t t = __funnelshift_l(lo32, w, 3);  // exponent + top 23 fraction bits
+  uint32_t hb = t | (hi32 & 0x80000000u);
+  float xh = __uint_as_float(hb);
+  float m = __uint2float_rn(lo32 & 0x1FFFFFFFu);                        // low 29 bits
+  float pw = __fmul_rn(__uint_as_float(hb & 0xFF800000u), 0x1p-52f);    // +-2^(E-52)
+  return df{xh, __fmul_rn(m, pw)};
+}
+
+__device__ __forceinline__ df df_split(double x) {
+  return df_split_bits((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
+}
+
+// (S, lo) with |lo| << |S| (not necessarily normalised) -> FP64.
+__device__ __forceinline__ double df_to_double(float S, float lo) {
+  float s = __fadd_rz(S, lo);          // toward zero: the remainder shares s's sign
+  float z = __fsub_rn(s, S);
+  float e = __fsub_rn(lo, z);
+  uint32_t fs = __float_as_uint(s);
+  uint32_t fa = fs & 0x7FFFFFFFu;
+  uint32_t sg = fs & 0x80000000u;
+  float pw = __uint_as_float((306u << 23) - (fa & 0x7F800000u));        // 2^(52 - E_s)
+  uint32_t low29 = min(__float2uint_rz(__fmul_rn(fabsf(e), pw)), 0x1FFFFFFFu);
+  uint32_t hiw = ((fa >> 3) + 0x38000000u) | sg;
+  hiw = fa ? hiw : sg;
+  uint32_t low = fa ? ((fs << 29) | low29) : 0u;
+  return __hiloint2double((int)hiw, (int)low);
+}
+
+// Normalise (S, lo) into a pair usable as an operand: Fast2Sum.
+__device__ __forceinline__ df df_norm(float S, float lo) {
+  float h = __fadd_rn(S, lo);
+  float l = __fsub_rn(lo, __fsub_rn(h, S));
+  return df{h, l};
+}
+
+// ------------------------------------------------------------- MathF64
+struct MathF64 {
+  using R = double;   // one real component
+  using A = double;   // accumulator
+  static constexpr bool kNative64 = true;
+  __device__ static __forceinline__ R from_f64(double x) { return x; }
+  __device__ static __forceinline__ double to_f64(const A& a) { return a; }
+  __device__ static __forceinline__ R finish(const A& a) { return a; }
+  __device__ static __forceinline__ A to_acc(const R& x) { return x; }
+  __device__ static __forceinline__ A zero() { return 0.0; }
+  __device__ static __forceinline__ R neg(const R& x) { return -x; }
+  __device__ static __forceinline__ R scalar(double s, float, float) { return s; }
+  // a (+)= sg * x * y ; FIRST: a = sg * x * y
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void fma(A& a, const R& x, const R& y) {
+    if (FIRST) a = (SG > 0) ? __dmul_rn(x, y) : __dmul_rn(-x, y);
+    else a = (SG > 0) ? __fma_rn(x, y, a) : __fma_rn(-x, y, a);
+  }
+  // a (+)= sg * x
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void add(A& a, const R& x) {
+    if (FIRST) a = (SG > 0) ? x : -x;
+    else a = (SG > 0) ? __dadd_rn(a, x) : __dsub_rn(a, x);
+  }
+};
+
+// -------------------------------------------------------------- MathDF
+struct DAcc {
+  float S, lo;
+};
+
+struct MathDF {
+  using R = df;
+  using A = DAcc;
+  static constexpr bool kNative64 = false;
+  __device__ static __forceinline__ R from_f64(double x) { return df_split(x); }
+  __device__ static __forceinline__ double to_f64(const A& a) { return df_to_double(a.S, a.lo); }
+  __device__ static __forceinline__ R finish(const A& a) { return df_norm(a.S, a.lo); }
+  __device__ static __forceinline__ A to_acc(const R& x) { return DAcc{x.h, x.l}; }
+  __device__ static __forceinline__ A zero() { return DAcc{0.0f, 0.0f}; }
+  __device__ static __forceinline__ R neg(const R& x) { return df{-x.h, -x.l}; }
+  __device__ static __forceinline__ R scalar(double, float sh, float sl) { return df{sh, sl}; }
+
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void fma(A& a, const R& x0, const R& y) {
+    const float xh = SG > 0 ? x0.h : -x0.h;
+    const float xl = SG > 0 ? x0.l : -x0.l;
+    const float p = __fmul_rn(xh, y.h);
+    if (FIRST) {
+      float q = __fmaf_rn(xh, y.h, -p);       // exact error of the leading product
+      q = __fmaf_rn(xh, y.l, q);
+      q = __fmaf_rn(xl, y.h, q);
+      a.S = p;
+      a.lo = q;
+    } else {
+      const float s = __fadd_rn(a.S, p);       // TwoSum(S, xh*yh)
+      const float bp = __fsub_rn(s, a.S);
+      const float ap = __fsub_rn(s, bp);
+      const float db = __fmaf_rn(xh, y.h, -bp);  // exact product minus bp, one rounding
+      const float da = __fsub_rn(a.S, ap);
+      float lo = __fadd_rn(a.lo, da);
+      lo = __fadd_rn(lo, db);
+      lo = __fmaf_rn(xh, y.l, lo);
+      lo = __fmaf_rn(xl, y.h, lo);
+      a.S = s;
+      a.lo = lo;
+    }
+  }
+
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void add(A& a, const R& x0) {
+    const float xh = SG > 0 ? x0.h : -x0.h;
+    const float xl = SG > 0 ? x0.l : -x0.l;
+    if (FIRST) {
+      a.S = xh;
+      a.lo = xl;
+    } else {
+      const float s = __fadd_rn(a.S, xh);
+      const float bp = __fsub_rn(s, a.S);
+      const float ap = __fsub_rn(s, bp);
+      const float db = __fsub_rn(xh, bp);
+      const float da = __fsub_rn(a.S, ap);
+      float lo = __fadd_rn(a.lo, da);
+      lo = __fadd_rn(lo, db);
+      lo = __fadd_rn(lo, xl);
+      a.S = s;
+      a.lo = lo;
+    }
+  }
+};
+
+// ------------------------------------------------------------- MathF32
+struct MathF32 {
+  using R = float;
+  using A = float;
+  static constexpr bool kNative64 = false;
+  __device__ static __forceinline__ R finish(const A& a) { return a; }
+  __device__ static __forceinline__ A to_acc(const R& x) { return x; }
+  __device__ static __forceinline__ A zero() { return 0.0f; }
+  __device__ static __forceinline__ R neg(const R& x) { return -x; }
+  __device__ static __forceinline__ R scalar(double, float sh, float) { return sh; }
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void fma(A& a, const R& x, const R& y) {
+    if (FIRST) a = (SG > 0) ? __fmul_rn(x, y) : __fmul_rn(-x, y);
+    else a = (SG > 0) ? __fmaf_rn(x, y, a) : __fmaf_rn(-x, y, a);
+  }
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void add(A& a, const R& x) {
+    if (FIRST) a = (SG > 0) ? x : -x;
+    else a = (SG > 0) ? __fadd_rn(a, x) : __fsub_rn(a, x);
+  }
+};
+
+}  // namespace su3s

@@ -1,0 +1,45 @@
+// Plain-data kernel parameters shared by host planning code and kernels.
+#pragma once
+
+#include <stdint.h>
+
+namespace su3s {
+
+enum Prec { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_F16 = 3, P_F64_C12 = 4, P_F32_C12 = 5 };
+enum Kind { K_MATRIX = 0, K_VECTOR = 1, K_REAL = 2 };
+enum MathId { MATH_F64 = 1, MATH_DF = 2, MATH_F32 = 3 };
+
+constexpr int kMaxLeaves = 6;
+constexpr int kMaxScalars = 4;
+
+// Addressing of one field: element (site s, link mu, component c) is at
+//   (s >> logB) * s_blk + mu * s_mu + c * s_c + (s & mask)
+// in units of one stored complex (one real for real fields).
+struct FieldDesc {
+  void* ptr;
+  int64_t s_blk;
+  int64_t s_mu;
+  int64_t s_c;
+  int32_t logB;
+  uint32_t mask;
+};
+
+struct KParams {
+  FieldDesc leaf[kMaxLeaves];
+  FieldDesc dst;
+  double sc[kMaxScalars];   // real factors of scale nodes, in tree order
+  float sch[kMaxScalars];   // sc split into FP32 pairs (pair arithmetic)
+  float scl[kMaxScalars];
+  int64_t nvec;             // site vectors per link (= Vpad / sites per vector)
+  int32_t nmu;
+};
+
+// Adjoint kernels: leaf fields are read, grad_out is read, leaf gradients
+// written (ptr == nullptr: skipped).
+struct GParams {
+  KParams k;                  // leaves, scalars, sizes (k.dst unused)
+  FieldDesc gout;             // dL/dZ
+  FieldDesc gleaf[kMaxLeaves];
+};
+
+}  // namespace su3s

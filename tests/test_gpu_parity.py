@@ -1,0 +1,561 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Tolerances:
+  * FP64 storage (native FP64 or pair-of-FP32 arithmetic): 1e-13 per real
+    component for products of SU(3) matrices (sum_t |x_t y_t| <= 1 there); for
+    Gaussian operands the same bound scaled by max(1, sum_t |x_t y_t|).
+  * FP32/BF16/FP16 storage with FP32 accumulation: against the oracle that
+    rounds the inputs to the format, multiplies in FP64 and rounds the output,
+    at most one unit in the last place of the output format plus 8*2^-24.
+  * Integer/layout work (pack/unpack, copies): bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import E1, E2, E3, cplx, lattice_fields
+
+pytestmark = pytest.mark.gpu
+
+SEED = synth.SEED_BASE
+TOL = 1e-13
+DIMS = [(1, 1, 1, 1), (2, 2, 2, 2), (3, 2, 1, 5), (6, 5, 7, 3), (8, 8, 8, 8)]
+LAYOUTS = [("soa", 0, 0), ("aosoa4", 1, 4), ("aosoa32", 1, 32), ("aosoa128", 1, 128)]
+
+
+def layout_id(x):
+    return x[0]
+
+
+@pytest.fixture(scope="module")
+def su3s(gpu_lib):
+    return gpu_lib
+
+
+def upload(su3s, lat, arr, kind=None, nmu=1, prec=None, layout=0, block=0):
+    kind = su3s.MATRIX if kind is None else kind
+    prec = su3s.F64 if prec is None else prec
+    f = su3s.Field(lat, kind, nmu, prec, layout, block or 64)
+    f.upload(arr)
+    return f
+
+
+def tree_expr(tree, fields):
+    op = tree[0]
+    if op == "leaf":
+        return fields[tree[1]].expr()
+    if op == "mul":
+        return tree_expr(tree[1], fields) * tree_expr(tree[2], fields)
+    if op == "add":
+        return tree_expr(tree[1], fields) + tree_expr(tree[2], fields)
+    if op == "sub":
+        return tree_expr(tree[1], fields) - tree_expr(tree[2], fields)
+    if op == "scale":
+        return float(tree[1]) * tree_expr(tree[2], fields)
+    return tree_expr(tree[1], fields).adj()
+
+
+# ------------------------------------------------------------------ products
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("lay", LAYOUTS, ids=layout_id)
+@pytest.mark.parametrize("dims", DIMS, ids=str)
+def test_mm(su3s, dims, lay, math):
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED)
+    a = upload(su3s, lat, f["a"], layout=lay[1], block=lay[2])
+    b = upload(su3s, lat, f["b"], layout=lay[1], block=lay[2])
+    z = a.like()
+    su3s.evaluate(z, a * b, math)
+    err = np.abs(z.download() - oracle.mm(f["a"], f["b"])).max()
+    assert err < TOL
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("lay", LAYOUTS[:2], ids=layout_id)
+@pytest.mark.parametrize("dims", [(3, 2, 1, 5), (8, 8, 8, 8)], ids=str)
+def test_mv(su3s, dims, lay, math):
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, names=("a", "v"))
+    a = upload(su3s, lat, f["a"], layout=lay[1], block=lay[2])
+    v = upload(su3s, lat, f["v"], kind=su3s.VECTOR, layout=lay[1], block=lay[2])
+    z = v.like()
+    su3s.evaluate(z, a * v, math)
+    ref = oracle.mv(f["a"], f["v"])
+    scale = max(1.0, np.abs(cplx(f["v"])).sum(axis=1).max())
+    assert np.abs(z.download() - ref).max() < TOL * scale
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2]], ids=layout_id)
+def test_lorentz_links(su3s, lay, math):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, nmu=4)
+    a = upload(su3s, lat, f["a"], nmu=4, layout=lay[1], block=lay[2])
+    b = upload(su3s, lat, f["b"], nmu=4, layout=lay[1], block=lay[2])
+    z = a.like()
+    su3s.evaluate(z, a * b, math)
+    assert np.abs(z.download() - oracle.mm(f["a"], f["b"])).max() < TOL
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+def test_gaussian_operands(su3s, math):
+    dims = (6, 5, 7, 3)
+    v = synth.volume(dims)
+    lat = su3s.Lattice(dims)
+    ga, gb = synth.gauss_matrix(SEED, 0, v), synth.gauss_matrix(SEED, 1, v)
+    a, b = upload(su3s, lat, ga), upload(su3s, lat, gb)
+    z = a.like()
+    su3s.evaluate(z, a * b, math)
+    scale = np.einsum("nij,njk->nik", np.abs(cplx(ga)), np.abs(cplx(gb)))   # sum_j |a_ij||b_jk|
+    err = np.abs(cplx(z.download()) - cplx(oracle.mm(ga, gb)))
+    assert (err <= TOL * np.maximum(1.0, 2 * scale)).all()
+
+
+def test_dest_aliases_leaf(su3s):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED)
+    a, b = upload(su3s, lat, f["a"]), upload(su3s, lat, f["b"])
+    su3s.evaluate(b, a * b)          # b <- a*b in place
+    assert np.abs(b.download() - oracle.mm(f["a"], f["b"])).max() < TOL
+
+
+def test_zero_and_identity_inputs(su3s):
+    dims = (3, 2, 1, 5)
+    lat = su3s.Lattice(dims)
+    v = synth.volume(dims)
+    eye = np.zeros((v, 3, 3, 2))
+    eye[:, [0, 1, 2], [0, 1, 2], 0] = 1.0
+    f = lattice_fields(dims, SEED)
+    for math in (1, 2):
+        a, i = upload(su3s, lat, f["a"]), upload(su3s, lat, eye)
+        z = a.like()
+        su3s.evaluate(z, a * i, math)
+        if math == 1:   # native FP64: multiplying by the identity is exact
+            assert np.array_equal(z.download() + 0.0, f["a"] + 0.0)
+        else:           # pair arithmetic carries ~48 significant bits
+            assert np.abs(z.download() - f["a"]).max() <= 2.0 ** -46
+        zero = upload(su3s, lat, np.zeros_like(eye))
+        su3s.evaluate(z, a * zero, math)
+        assert np.array_equal(z.download() + 0.0, np.zeros_like(eye))
+
+
+# -------------------------------------------------------------- fused trees
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("name,tree", [("E1", E1), ("E2", E2), ("E3", E3)], ids=["E1", "E2", "E3"])
+@pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2]], ids=layout_id)
+def test_fused_trees(su3s, name, tree, lay, math):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    names = oracle.leaf_names(tree)
+    f = lattice_fields(dims, SEED, names=tuple(names))
+    fields = {n: upload(su3s, lat, f[n], layout=lay[1], block=lay[2]) for n in names}
+    e = tree_expr(tree, fields)
+    assert e.signature() in {s for (_, s, p, m) in su3s.catalogue() if p == "f64"}
+    z = fields[names[0]].like()
+    su3s.evaluate(z, e, math)
+    ref = oracle.eval_tree(tree, f)
+    assert np.abs(z.download() - ref).max() < TOL * 2
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+def test_fused_equals_term_by_term_on_gpu(su3s, math):
+    dims = (8, 8, 8, 8)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, names=("a", "b", "c", "d"))
+    F = {n: upload(su3s, lat, f[n]) for n in "abcd"}
+    fused, t1, t2, tot = (F["a"].like() for _ in range(4))
+    su3s.evaluate(fused, F["a"] * F["b"] + F["c"] * F["d"], math)
+    su3s.evaluate(t1, F["a"] * F["b"], math)
+    su3s.evaluate(t2, F["c"] * F["d"], math)
+    su3s.evaluate(tot, t1 + t2, math)
+    # two evaluations compared with each other: each is within the FP64
+    # tolerance of the exact value
+    tol = 2e-15 if math == 1 else TOL
+    assert np.abs(fused.download() - tot.download()).max() < tol
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+def test_interpreter_for_uncatalogued_trees(su3s, math):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, names=("a", "b", "c", "d", "v"))
+    F = {n: upload(su3s, lat, f[n], kind=(su3s.VECTOR if n == "v" else su3s.MATRIX)) for n in "abcdv"}
+    trees = [
+        ("sub", ("mul", ("add", ("mul", ("leaf", "a"), ("leaf", "b")), ("leaf", "c")),
+                 ("adj", ("leaf", "d"))), ("scale", 2.5, ("leaf", "a"))),
+        ("mul", ("adj", ("mul", ("leaf", "a"), ("leaf", "b"))), ("leaf", "v")),
+        ("add", ("scale", -0.25, ("mul", ("leaf", "c"), ("leaf", "v"))),
+         ("mul", ("leaf", "d"), ("mul", ("leaf", "a"), ("leaf", "v")))),
+    ]
+    cat = {s for (_, s, p, m) in su3s.catalogue()}
+    for tree in trees:
+        e = tree_expr(tree, F)
+        assert e.signature() not in cat
+        kind = su3s.VECTOR if tree[0] != "sub" else su3s.MATRIX
+        z = F["v"].like() if kind == su3s.VECTOR else F["a"].like()
+        su3s.evaluate(z, e, math)
+        leaves = {n: f[n] for n in oracle.leaf_names(tree)}
+        ref = oracle.eval_tree(tree, leaves)
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(z.download() - ref).max() < 4 * TOL * scale
+
+
+def test_listing2_real_fields(su3s):
+    import os
+    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                   "listing2.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    dims = (6, 5, 7, 3)
+    v = synth.volume(dims)
+    lat = su3s.Lattice(dims)
+    for math in (1, 2):
+        for v1, v2, expr, v3 in rows:
+            f1 = upload(su3s, lat, np.full(v, float(v1)), kind=su3s.REAL)
+            f2 = upload(su3s, lat, np.full(v, float(v2)), kind=su3s.REAL)
+            out = f1.like()
+            e = f1 + f2 if expr == "v1+v2" else f1 + f2 + f1 * f2
+            su3s.evaluate(out, e, math)
+            assert np.array_equal(out.download(), np.full(v, float(v3)))
+
+
+def test_real_field_trees_random(su3s):
+    dims = (6, 5, 7, 3)
+    v = synth.volume(dims)
+    lat = su3s.Lattice(dims)
+    r1, r2 = synth.uniform_real(SEED, 6, v), synth.uniform_real(SEED, 7, v)
+    a, b = upload(su3s, lat, r1, kind=su3s.REAL), upload(su3s, lat, r2, kind=su3s.REAL)
+    tree = ("add", ("add", ("leaf", "x"), ("leaf", "y")), ("mul", ("leaf", "x"), ("leaf", "y")))
+    ref = oracle.eval_tree(tree, {"x": r1, "y": r2})
+    for math in (1, 2):
+        z = a.like()
+        su3s.evaluate(z, a + b + a * b, math)
+        assert np.abs(z.download() - ref).max() < TOL
+
+
+# ---------------------------------------------------------- reduced precision
+ULP = {"f32": lambda x: np.spacing(np.abs(x).astype(np.float32)).astype(np.float64),
+       "f16": lambda x: np.spacing(np.abs(x).astype(np.float16)).astype(np.float64),
+       "bf16": lambda x: 2.0 ** (np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** -126))) - 7)}
+BOUND_VS_F64 = {"f32": 2e-6, "f16": 3e-3, "bf16": 2.5e-2}
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[1], LAYOUTS[2]], ids=layout_id)
+@pytest.mark.parametrize("dims", [(3, 2, 1, 5), (8, 8, 8, 8), (16, 16, 16, 32)], ids=str)
+def test_reduced_precision_mm(su3s, fmt, lay, dims):
+    prec = {"f32": su3s.F32, "bf16": su3s.BF16, "f16": su3s.F16}[fmt]
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED)
+    a = upload(su3s, lat, f["a"], prec=prec, layout=lay[1], block=lay[2])
+    b = upload(su3s, lat, f["b"], prec=prec, layout=lay[1], block=lay[2])
+    z = a.like()
+    su3s.evaluate(z, a * b)
+    got = z.download()
+    # oracle (i): inputs rounded to the format, FP64 product, output rounded
+    ref_i = oracle.round_to(oracle.mm(oracle.round_to(f["a"], fmt), oracle.round_to(f["b"], fmt)), fmt)
+    assert (np.abs(got - ref_i) <= ULP[fmt](ref_i) + 8 * 2.0 ** -24).all()
+    # (ii) against the exact FP64 product: the a priori bound
+    err = np.abs(got - oracle.mm(f["a"], f["b"])).max()
+    assert err < BOUND_VS_F64[fmt]
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16", "f16"])
+def test_reduced_precision_mv(su3s, fmt):
+    prec = {"f32": su3s.F32, "bf16": su3s.BF16, "f16": su3s.F16}[fmt]
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, names=("a", "v"))
+    vv = f["v"] / 4.0   # keep FP16 far from overflow
+    a = upload(su3s, lat, f["a"], prec=prec)
+    v = upload(su3s, lat, vv, kind=su3s.VECTOR, prec=prec)
+    z = v.like()
+    su3s.evaluate(z, a * v)
+    ref_i = oracle.round_to(oracle.mv(oracle.round_to(f["a"], fmt), oracle.round_to(vv, fmt)), fmt)
+    assert (np.abs(z.download() - ref_i) <= ULP[fmt](ref_i) + 8 * 2.0 ** -24).all()
+
+
+# ------------------------------------------------------------- two-row SU(3)
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2]], ids=layout_id)
+def test_c12_f64(su3s, lay, math):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED)
+    a = upload(su3s, lat, f["a"], prec=su3s.F64_C12, layout=lay[1], block=lay[2])
+    b = upload(su3s, lat, f["b"], prec=su3s.F64_C12, layout=lay[1], block=lay[2])
+    z = a.like()
+    su3s.evaluate(z, a * b, math)
+    got = z.download()
+    ea, eb = (oracle.c12_expand(f[n][:, :2].copy()) for n in "ab")
+    ref = oracle.mm(ea, eb)
+    assert np.abs(got[:, :2] - ref[:, :2]).max() < TOL            # stored rows
+    assert np.abs(got - oracle.c12_expand(ref[:, :2].copy())).max() < TOL
+    assert np.abs(got - oracle.mm(f["a"], f["b"])).max() < 1e-12
+
+
+def test_c12_f32(su3s):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED)
+    a = upload(su3s, lat, f["a"], prec=su3s.F32_C12)
+    b = upload(su3s, lat, f["b"], prec=su3s.F32_C12)
+    z = a.like()
+    su3s.evaluate(z, a * b)
+    got = z.download()
+    ra, rb = (oracle.round_to(f[n][:, :2].copy(), "f32") for n in "ab")
+    ref = oracle.mm(oracle.c12_expand(ra), oracle.c12_expand(rb))
+    # FP32 rebuild + FP32 accumulation: a few FP32 ulps of O(1) values
+    assert np.abs(got[:, :2] - ref[:, :2]).max() < 3e-6
+    assert np.abs(got - oracle.mm(f["a"], f["b"])).max() < 5e-6
+
+
+# --------------------------------------------------------- pack and unpack
+@pytest.mark.parametrize("prec,fmt", [(0, None), (1, "f32"), (2, "bf16"), (3, "f16")],
+                         ids=["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("lay", LAYOUTS, ids=layout_id)
+def test_pack_unpack_roundtrip(su3s, prec, fmt, lay):
+    dims = (3, 2, 1, 5)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, nmu=4, names=("a", "v"))
+    for kind, arr in ((su3s.MATRIX, f["a"]), (su3s.VECTOR, f["v"])):
+        x = upload(su3s, lat, arr, kind=kind, nmu=4, prec=prec, layout=lay[1], block=lay[2])
+        want = arr if fmt is None else oracle.round_to(arr, fmt)
+        assert np.array_equal(x.download(), want)
+        dev = torch.from_numpy(arr.copy()).cuda()
+        y = x.like()
+        y.pack(dev)
+        assert torch.equal(y.unpack().cpu(), torch.from_numpy(want))
+
+
+def test_pack_zeroes_pad_sites(su3s):
+    dims = (3, 2, 1, 5)   # 30 sites, padded to 64
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED)
+    x = su3s.Field(lat, su3s.MATRIX, 1, su3s.F64, su3s.SOA)
+    x.tensor.fill_(float("nan"))
+    x.upload(f["a"])
+    t = x.tensor.view(9, 64, 2)
+    assert torch.all(t[:, 30:, :] == 0)
+    assert not torch.isnan(t[:, :30, :]).any()
+
+
+# ---------------------------------------------------------- reverse mode
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("name,tree", [("MM", ("mul", ("leaf", "a"), ("leaf", "b"))), ("E1", E1),
+                                       ("E2", E2), ("E3", E3)], ids=["MM", "E1", "E2", "E3"])
+def test_adjoint_kernels(su3s, name, tree, math):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    names = oracle.leaf_names(tree)
+    f = lattice_fields(dims, SEED, names=tuple(names) + ("w",))
+    F = {n: upload(su3s, lat, f[n]) for n in names}
+    G = upload(su3s, lat, f["w"])
+    grads = [F[n].like() for n in names]
+    su3s.eval_adjoint(tree_expr(tree, F), G, grads, math)
+    ref = oracle.eval_adjoint(tree, {n: f[n] for n in names}, f["w"])
+    wscale = np.abs(f["w"]).max() * 3
+    for n, g in zip(names, grads):
+        assert np.abs(g.download() - ref[n]).max() < TOL * wscale, n
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+def test_adjoint_matrix_vector(su3s, math):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    v = synth.volume(dims)
+    f = lattice_fields(dims, SEED, names=("a", "v"))
+    gz = synth.gauss_vector(SEED, 9, v)
+    a = upload(su3s, lat, f["a"])
+    x = upload(su3s, lat, f["v"], kind=su3s.VECTOR)
+    G = upload(su3s, lat, gz, kind=su3s.VECTOR)
+    ga, gv = a.like(), x.like()
+    su3s.eval_adjoint(a * x, G, [ga, gv], math)
+    ref = oracle.eval_adjoint(("mul", ("leaf", "a"), ("leaf", "v")), f, gz)
+    s = np.abs(gz).max() * np.abs(f["v"]).max() * 6
+    assert np.abs(ga.download() - ref["a"]).max() < TOL * s
+    assert np.abs(gv.download() - ref["v"]).max() < TOL * s
+
+
+def test_autograd_gradient_16x4(su3s):
+    """L = sum_x Re tr(W^dagger (a*b)) on a 16^4 lattice: gradients against the
+    oracle's closed form and against central finite differences."""
+    dims = (16, 16, 16, 16)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, synth.SEED_BASE + 4, names=("a", "b", "w"))
+    a, b, w = (upload(su3s, lat, f[n]) for n in "abw")
+    ta = a.tensor.clone().requires_grad_(True)
+    tb = b.tensor.clone().requires_grad_(True)
+    z = su3s.lattice_expr(("mul", ("leaf", 0), ("leaf", 1)), lat, [ta, tb])
+    loss = (w.tensor * z).sum()   # pad sites of W are zero
+    loss.backward()
+    ga = su3s.Field(lat, tensor=ta.grad.contiguous()).download()
+    gb = su3s.Field(lat, tensor=tb.grad.contiguous()).download()
+    ref = oracle.eval_adjoint(("mul", ("leaf", "a"), ("leaf", "b")), f, f["w"])
+    assert np.abs(ga - ref["a"]).max() < TOL * 8
+    assert np.abs(gb - ref["b"]).max() < TOL * 8
+    # the loss itself against the oracle
+    lo = oracle.redot(f["w"], oracle.mm(f["a"], f["b"]))
+    assert abs(loss.item() - lo) <= 1e-11 * abs(lo) + 1e-9
+    # central differences on 64 random real components of a and b (L is linear
+    # in each, so the difference quotient is exact up to rounding)
+    rng = np.random.default_rng(11)
+    h = 1e-3
+    zf = a.like()
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    for name, grad in (("a", ga), ("b", gb)):
+        flat = f[name].reshape(-1)
+        for k in rng.choice(flat.size, 32, replace=False):
+            vals = []
+            for sgn in (1, -1):
+                pert = f[name].copy()
+                pert.reshape(-1)[k] += sgn * h
+                x = upload(su3s, lat, pert)
+                su3s.evaluate(zf, (x * b) if name == "a" else (a * x), su3s.MATH_F64)
+                vals.append(su3s.redot(w, zf, out).item())
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - grad.reshape(-1)[k]) < 1e-7 * max(1.0, abs(lo)) ** 0.5
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+def test_autograd_fused_tree(su3s, math):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, names=("a", "b", "c", "d", "w"))
+    F = {n: upload(su3s, lat, f[n]) for n in "abcdw"}
+    ts = [F[n].tensor.clone().requires_grad_(True) for n in "abcd"]
+    tree = ("add", ("mul", ("leaf", 0), ("leaf", 1)), ("mul", ("leaf", 2), ("leaf", 3)))
+    z = su3s.lattice_expr(tree, lat, ts, math=math)
+    (F["w"].tensor * z).sum().backward()
+    ref = oracle.eval_adjoint(E1, {n: f[n] for n in "abcd"}, f["w"])
+    for n, t in zip("abcd", ts):
+        g = su3s.Field(lat, tensor=t.grad.contiguous()).download()
+        assert np.abs(g - ref[n]).max() < TOL * 16
+
+
+# --------------------------------------------------------- batched launches
+def config4_volumes(seed, n=64):
+    shapes = [(4, 4, 4, 4), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 24)]
+    picks = (synth.uniform_real(seed, 40, n) + 1.0) / 2.0 * len(shapes)
+    return [shapes[min(int(p), len(shapes) - 1)] for p in picks]
+
+
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+def test_batch_matches_separate_evaluations(su3s, math):
+    seed = synth.SEED_BASE + 4
+    shapes = config4_volumes(seed, 12)
+    items = []
+    b = su3s.Batch()
+    for i, dims in enumerate(shapes):
+        lat = su3s.Lattice(dims)
+        v = synth.volume(dims)
+        host = {n: synth.su3(seed + 1000 * i, synth.FIELD[n], v) for n in "abcd"}
+        F = {n: upload(su3s, lat, host[n]) for n in "abcd"}
+        z = F["a"].like()
+        b.add(z, F["a"] * F["b"] + F["c"] * F["d"])
+        items.append((lat, host, F, z))
+    # one extra item the persistent kernel does not cover (interpreter inside the graph)
+    _, host0, F0, _ = items[0]
+    zi = F0["a"].like()
+    b.add(zi, (F0["a"] + F0["b"]) * F0["c"].adj())
+    b.build(math)
+    for _ in range(2):
+        b.launch()
+    torch.cuda.synchronize()
+    for lat, host, F, z in items:
+        ref = oracle.mm(host["a"], host["b"]) + oracle.mm(host["c"], host["d"])
+        got = z.download()
+        assert np.abs(got - ref).max() < 2 * TOL
+        sep = z.like()
+        su3s.evaluate(sep, F["a"] * F["b"] + F["c"] * F["d"], math)
+        assert np.array_equal(sep.download(), got)   # same arithmetic, same bits
+    ref = oracle.eval_tree(("mul", ("add", ("leaf", "a"), ("leaf", "b")), ("adj", ("leaf", "c"))),
+                           host0)
+    assert np.abs(zi.download() - ref).max() < 4 * TOL
+    sites, tiles = b.info()
+    assert sites > 0 and tiles > 0
+
+
+# ---------------------------------------------------------- tuning
+def test_launch_geometry_does_not_change_results(su3s):
+    dims = (8, 8, 8, 8)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, names=("a", "b", "c", "d"))
+    F = {n: upload(su3s, lat, f[n]) for n in "abcd"}
+    e = F["a"] * F["b"] + F["c"] * F["d"]
+    outs = []
+    for math in (1, 2):
+        ref = None
+        for th, bps in ((64, 0), (128, 2), (256, 0), (256, 8), (96, 1)):
+            z = F["a"].like()
+            su3s.set_launch(z, e, th, bps, math)
+            su3s.evaluate(z, e, math)
+            got = z.download()
+            if ref is None:
+                ref = got
+            assert np.array_equal(got, ref)
+        th, bps, ms = su3s.tune(z, e, math)
+        su3s.evaluate(z, e, math)
+        assert np.array_equal(z.download(), ref) and th in (64, 128, 256) and ms > 0
+        outs.append(ref)
+
+
+# --------------------------------------------------- reductions, projection
+def test_redot(su3s):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, nmu=4, names=("a", "w"))
+    a, w = upload(su3s, lat, f["a"], nmu=4), upload(su3s, lat, f["w"], nmu=4)
+    got = su3s.redot(a, w).item()
+    want = oracle.redot(f["a"], f["w"])
+    assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+    # deterministic
+    assert su3s.redot(a, w).item() == got
+
+
+@pytest.mark.parametrize("prec,fmt,tol", [(0, None, 1e-13), (1, "f32", 1e-6)], ids=["f64", "f32"])
+def test_reunitarize(su3s, prec, fmt, tol):
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    v = synth.volume(dims)
+    noisy = synth.su3(SEED, 0, v) + 1e-3 * synth.gauss_matrix(SEED, 5, v)
+    x = upload(su3s, lat, noisy, prec=prec)
+    y = x.like()
+    su3s.reunitarize(y, x)
+    src = noisy if fmt is None else oracle.round_to(noisy, fmt)
+    ref = oracle.reunitarize(src)
+    if fmt is not None:
+        ref = oracle.round_to(ref, fmt)
+    assert np.abs(y.download() - ref).max() < tol
+    u = cplx(y.download())
+    assert np.abs(u @ np.conj(np.swapaxes(u, 1, 2)) - np.eye(3)).max() < max(tol, 1e-13) * 10
+
+
+# ------------------------------------------------------ full-size sampling
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+def test_full_size_48_sampled(su3s, math):
+    """The 48^4 configuration in the launch geometry the benchmark uses:
+    z=a*b, z=a*v and Lorentz z_mu=a_mu*b_mu checked on sampled sites."""
+    dims = (48, 48, 48, 48)
+    v = synth.volume(dims)
+    seed = synth.SEED_BASE + 1
+    lat = su3s.Lattice(dims)
+    rng = np.random.default_rng(2)
+    sample = np.unique(np.concatenate([rng.choice(v, 3000, replace=False), [0, v - 1]]))
+    for nmu, vec in ((1, False), (1, True), (4, False)):
+        ha = synth.su3(seed, 0, v * nmu)
+        hb = synth.gauss_vector(seed, 4, v * nmu) if vec else synth.su3(seed, 1, v * nmu)
+        a = upload(su3s, lat, ha, nmu=nmu)
+        b = upload(su3s, lat, hb, kind=su3s.VECTOR if vec else su3s.MATRIX, nmu=nmu)
+        z = b.like()
+        su3s.evaluate(z, a * b, math)
+        idx = (sample[:, None] * nmu + np.arange(nmu)[None, :]).reshape(-1)
+        got = z.unpack()[torch.from_numpy(idx).cuda()].cpu().numpy()
+        ref = oracle.mv(ha[idx], hb[idx]) if vec else oracle.mm(ha[idx], hb[idx])
+        scale = 1.0 if not vec else max(1.0, np.abs(cplx(hb[idx])).sum(axis=1).max())
+        assert np.abs(got - ref).max() < TOL * scale
+        del a, b, z
+        torch.cuda.empty_cache()
