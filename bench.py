@@ -41,6 +41,11 @@ BATCH_SHAPES = [(4, 4, 4, 4), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), 
 B_MM, B_MV, B_E1, B_E2, B_E3 = 432, 240, 720, 720, 432
 B_F32, B_H, B_C12, B_C12F = 216, 108, 288, 144
 B_ADJ_MM, B_ADJ_E1 = 720, 1296
+ROW_NAMES = ["A2 z=a*b", "A3 z=a*v", "A4 z_mu=a_mu*b_mu", "A5 z=a*b+c*d", "A5 z=a*b*c+0.5*d",
+             "A5 z=adj(a)*b-b*adj(a)", "A6 z=a*b f32", "A6 z=a*b bf16", "A6 z=a*b f16",
+             "A7 z=a*b f64_c12", "A7 z=a*b f32_c12", "A8 batch 64 lattices z=a*b+c*d",
+             "A9 adjoint of z=a*b", "A9 adjoint of z=a*b+c*d"]
+ROW_A8, ROW_A9A, ROW_A9B = ROW_NAMES[11], ROW_NAMES[12], ROW_NAMES[13]
 
 
 def dist_env():
@@ -48,6 +53,21 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x, dist, device):
+    """Maximum of a per-rank scalar over all ranks (identity without a group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gbs(bytes_per_rank_step, ws, ms_per_step_max):
+    """Whole-job bandwidth: bytes of all ranks over the slowest rank's time."""
+    return bytes_per_rank_step * ws / (ms_per_step_max * 1e-3) / 1e9
 
 
 def read_peaks():
@@ -116,10 +136,11 @@ class Row:
         self.ms = []
 
 
-def build_rows(su3s, synth, torch, with_host):
-    """Allocate fields, fill them from the seeded generator, return the rows."""
-    v = synth.volume(DIMS)
-    lat = su3s.Lattice(DIMS)
+def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True):
+    """Allocate fields, fill them from the seeded generator, return the rows
+    whose names pass `want`."""
+    v = synth.volume(dims)
+    lat = su3s.Lattice(dims)
     F64, MATRIX, VECTOR = su3s.F64, su3s.MATRIX, su3s.VECTOR
     host = {}
 
@@ -142,21 +163,31 @@ def build_rows(su3s, synth, torch, with_host):
         return f
 
     H = {}
+    need = {"a": any(want(n) for n in ROW_NAMES if "A8" not in n),
+            "b": any(want(n) for n in ROW_NAMES if "A8" not in n),
+            "c": any(want(n) for n in ROW_NAMES if ("c*d" in n or "*c" in n) and "A8" not in n),
+            "v": want("A3 z=a*v"), "w": any(want(n) for n in ROW_NAMES if "A9" in n),
+            "l": want("A4 z_mu=a_mu*b_mu")}
     for n, fid in (("a", 0), ("b", 1), ("c", 2), ("d", 3)):
-        H[n] = gen("su3", fid, v)
-    H["v"] = gen("vec", 4, v)
-    H["w"] = gen("gm", 5, v)
-    H["la"] = gen("su3", 0, v, 4)
-    H["lb"] = gen("su3", 1, v, 4)
+        if need["c" if n in "cd" else n]:
+            H[n] = gen("su3", fid, v)
+    if need["v"]:
+        H["v"] = gen("vec", 4, v)
+    if need["w"]:
+        H["w"] = gen("gm", 5, v)
+    if need["l"]:
+        H["la"] = gen("su3", 0, v, 4)
+        H["lb"] = gen("su3", 1, v, 4)
     P = {k: pinned(a) for k, a in H.items()}
 
     def fields_for(prec, names=("a", "b", "c", "d")):
-        return {n: field(lat, MATRIX, 1, prec, H[n]) for n in names}
+        return {n: field(lat, MATRIX, 1, prec, H[n]) for n in names if n in H}
 
     Fd = fields_for(F64)
-    Fv = field(lat, VECTOR, 1, F64, H["v"])
-    Fw = field(lat, MATRIX, 1, F64, H["w"])
-    La, Lb = field(lat, MATRIX, 4, F64, H["la"]), field(lat, MATRIX, 4, F64, H["lb"])
+    Fv = field(lat, VECTOR, 1, F64, H["v"]) if "v" in H else None
+    Fw = field(lat, MATRIX, 1, F64, H["w"]) if "w" in H else None
+    La = field(lat, MATRIX, 4, F64, H["la"]) if "la" in H else None
+    Lb = field(lat, MATRIX, 4, F64, H["lb"]) if "lb" in H else None
     rows = []
 
     shared_out = {}
@@ -177,38 +208,51 @@ def build_rows(su3s, synth, torch, with_host):
         return Row(name, bps * v * dest.nmu, v * dest.nmu, run, ins, [(dest, out_pin(dest))],
                    dtype=dtype)
 
-    z = Fd["a"].like()
-    rows.append(mk("A2 z=a*b", B_MM, z, Fd["a"] * Fd["b"],
-                   [(Fd["a"], P["a"]), (Fd["b"], P["b"])]))
-    zv = Fv.like()
-    rows.append(mk("A3 z=a*v", B_MV, zv, Fd["a"] * Fv, [(Fd["a"], P["a"]), (Fv, P["v"])]))
-    zl = La.like()
-    rows.append(mk("A4 z_mu=a_mu*b_mu", B_MM, zl, La * Lb, [(La, P["la"]), (Lb, P["lb"])]))
-    z1, z2, z3 = Fd["a"].like(), Fd["a"].like(), Fd["a"].like()
-    a, b, c, d = (Fd[n] for n in "abcd")
-    rows.append(mk("A5 z=a*b+c*d", B_E1, z1, a * b + c * d,
-                   [(Fd[n], P[n]) for n in "abcd"]))
-    rows.append(mk("A5 z=a*b*c+0.5*d", B_E2, z2, a * b * c + 0.5 * d,
-                   [(Fd[n], P[n]) for n in "abcd"]))
-    rows.append(mk("A5 z=adj(a)*b-b*adj(a)", B_E3, z3, a.adj() * b - b * a.adj(),
-                   [(Fd[n], P[n]) for n in "ab"]))
+    if want("A2 z=a*b"):
+        z = Fd["a"].like()
+        rows.append(mk("A2 z=a*b", B_MM, z, Fd["a"] * Fd["b"],
+                       [(Fd["a"], P["a"]), (Fd["b"], P["b"])]))
+    if want("A3 z=a*v"):
+        zv = Fv.like()
+        rows.append(mk("A3 z=a*v", B_MV, zv, Fd["a"] * Fv, [(Fd["a"], P["a"]), (Fv, P["v"])]))
+    if want("A4 z_mu=a_mu*b_mu"):
+        zl = La.like()
+        rows.append(mk("A4 z_mu=a_mu*b_mu", B_MM, zl, La * Lb, [(La, P["la"]), (Lb, P["lb"])]))
+    if "a" in Fd:
+        a, b = Fd["a"], Fd["b"]
+    if "c" in Fd:
+        c, d = Fd["c"], Fd["d"]
+    if want("A5 z=a*b+c*d"):
+        rows.append(mk("A5 z=a*b+c*d", B_E1, a.like(), a * b + c * d,
+                       [(Fd[n], P[n]) for n in "abcd"]))
+    if want("A5 z=a*b*c+0.5*d"):
+        rows.append(mk("A5 z=a*b*c+0.5*d", B_E2, a.like(), a * b * c + 0.5 * d,
+                       [(Fd[n], P[n]) for n in "abcd"]))
+    if want("A5 z=adj(a)*b-b*adj(a)"):
+        rows.append(mk("A5 z=adj(a)*b-b*adj(a)", B_E3, a.like(), a.adj() * b - b * a.adj(),
+                       [(Fd[n], P[n]) for n in "ab"]))
     for prec, nm, bps in ((su3s.F32, "f32", B_F32), (su3s.BF16, "bf16", B_H), (su3s.F16, "f16", B_H),
                           (su3s.F64_C12, "f64_c12", B_C12), (su3s.F32_C12, "f32_c12", B_C12F)):
+        tag = "A7" if "c12" in nm else "A6"
+        name = "%s z=a*b %s" % (tag, nm)
+        if not want(name):
+            continue
         Fp = fields_for(prec, ("a", "b"))
         zp = Fp["a"].like()
-        tag = "A7" if "c12" in nm else "A6"
-        rows.append(mk("%s z=a*b %s" % (tag, nm), bps, zp, Fp["a"] * Fp["b"],
+        rows.append(mk(name, bps, zp, Fp["a"] * Fp["b"],
                        [(Fp["a"], P["a"]), (Fp["b"], P["b"])], dtype=nm))
 
     # A8: 64 lattices of mixed volumes, one graph launch
+    if not want(ROW_A8):
+        return _adjoint_rows(su3s, rows, want, v, Fd, Fw, P, out_pin), {"lat": lat}
     picks = (synth.uniform_real(SEED + 3, 40, 64) + 1.0) / 2.0 * len(BATCH_SHAPES)
     batch = su3s.Batch()
     bins, bouts, bsites = [], [], 0
     keep = []
     for i, p in enumerate(picks):
-        dims = BATCH_SHAPES[min(int(p), len(BATCH_SHAPES) - 1)]
-        bl = su3s.Lattice(dims)
-        nv = synth.volume(dims)
+        bdims = BATCH_SHAPES[min(int(p), len(BATCH_SHAPES) - 1)]
+        bl = su3s.Lattice(bdims)
+        nv = synth.volume(bdims)
         fs = {}
         for n in "abcd":
             arr = synth.su3(SEED + 3 + 1000 * i, synth.FIELD[n], nv)
@@ -224,28 +268,36 @@ def build_rows(su3s, synth, torch, with_host):
     def run_batch(stream):
         batch.launch(stream)
         return 1
-    rows.append(Row("A8 batch 64 lattices z=a*b+c*d", B_E1 * bsites, bsites, run_batch, bins, bouts))
+    rows.append(Row(ROW_A8, B_E1 * bsites, bsites, run_batch, bins, bouts))
     rows[-1].keep = (batch, keep)
 
-    # A9: reverse mode
-    ga, gb = a.like(), a.like()
+    return _adjoint_rows(su3s, rows, want, v, Fd, Fw, P, out_pin), {"lat": lat}
 
-    def run_adj(stream):
-        su3s.eval_adjoint(a * b, Fw, [ga, gb], su3s.MATH_DEFAULT, stream)
-        return 1
-    rows.append(Row("A9 adjoint of z=a*b", B_ADJ_MM * v, v, run_adj,
-                    [(a, P["a"]), (b, P["b"]), (Fw, P["w"])],
-                    [(ga, out_pin(ga)), (gb, out_pin(gb))]))
-    g4 = [a.like() for _ in range(4)]
-    e1 = a * b + c * d
 
-    def run_adj1(stream):
-        su3s.eval_adjoint(e1, Fw, g4, su3s.MATH_DEFAULT, stream)
-        return 1
-    rows.append(Row("A9 adjoint of z=a*b+c*d", B_ADJ_E1 * v, v, run_adj1,
-                    [(Fd[n], P[n]) for n in "abcd"] + [(Fw, P["w"])],
-                    [(g, out_pin(g)) for g in g4]))
-    return rows, {"lat": lat, "fields": (Fd, Fv, Fw, La, Lb), "host": H}
+def _adjoint_rows(su3s, rows, want, v, Fd, Fw, P, out_pin):
+    """A9: reverse mode of z=a*b and of z=a*b+c*d."""
+    if want(ROW_A9A):
+        a, b = Fd["a"], Fd["b"]
+        ga, gb = a.like(), a.like()
+
+        def run_adj(stream):
+            su3s.eval_adjoint(a * b, Fw, [ga, gb], su3s.MATH_DEFAULT, stream)
+            return 1
+        rows.append(Row(ROW_A9A, B_ADJ_MM * v, v, run_adj,
+                        [(a, P["a"]), (b, P["b"]), (Fw, P["w"])],
+                        [(ga, out_pin(ga)), (gb, out_pin(gb))]))
+    if want(ROW_A9B):
+        a, b, c, d = (Fd[n] for n in "abcd")
+        g4 = [a.like() for _ in range(4)]
+        e1 = a * b + c * d
+
+        def run_adj1(stream):
+            su3s.eval_adjoint(e1, Fw, g4, su3s.MATH_DEFAULT, stream)
+            return 1
+        rows.append(Row(ROW_A9B, B_ADJ_E1 * v, v, run_adj1,
+                        [(Fd[n], P[n]) for n in "abcd"] + [(Fw, P["w"])],
+                        [(g, out_pin(g)) for g in g4]))
+    return rows
 
 
 def time_step(rows, torch, stream, steps, warmup, per_row_events=True):
@@ -356,7 +408,22 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the native-FP64 timings reported beside the step")
+    ap.add_argument("--rows", default="",
+                    help="comma-separated row-name prefixes to run (default: every row)")
+    ap.add_argument("--dims", default="48,48,48,48", help="lattice extents (default 48^4)")
+    ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "tma", "tma_leaf"],
+                    help="data movement of FP64-storage kernels (default: the library's choice)")
     args = ap.parse_args()
+    dims = tuple(int(x) for x in args.dims.split(","))
+    if len(dims) == 1:
+        dims = dims * 4
+    prefixes = [p.strip() for p in args.rows.split(",") if p.strip()]
+
+    def want(name):
+        return not prefixes or any(name.startswith(p) for p in prefixes)
+    full = not prefixes and dims == DIMS
     ws, rank, local = dist_env()
 
     if args.impl == "reference":
@@ -388,9 +455,11 @@ def main():
     import paper_1710_09409_gb300 as su3s
     import synth
     su3s.load()
+    su3s.set_pipeline({"auto": su3s.PIPE_AUTO, "plain": su3s.PIPE_PLAIN, "tma": su3s.PIPE_TMA,
+                       "tma_leaf": su3s.PIPE_TMA_LEAF}[args.pipeline])
     stream = torch.cuda.Stream()
     with_host = not args.no_e2e
-    rows, keep = build_rows(su3s, synth, torch, with_host)
+    rows, keep = build_rows(su3s, synth, torch, with_host, dims, want)
     torch.cuda.synchronize()
 
     # device-resident timing
@@ -405,12 +474,10 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     ms_step = total_ms / args.steps
     bytes_step = sum(r.nbytes for r in rows)
-    value = bytes_step * ws / (ms_step * 1e-3) / 1e9
+    value = aggregate_gbs(bytes_step, ws, ms_step)
 
     row_out = []
     for r, ms in zip(rows, per_row):
@@ -433,7 +500,7 @@ def main():
     # native FP64 arithmetic for the FP64 rows, reported beside (not in the step)
     variants = []
     su3s.set_default_math(su3s.MATH_F64)
-    for r in rows:
+    for r in (rows if not args.no_variants else []):
         if r.dtype == "f64" and not r.name.startswith("A8"):
             _, pr, _ = time_step([r], torch, stream, 20, 2)
             m = float(np.mean(pr[0]))
@@ -444,11 +511,8 @@ def main():
     e2e = None
     if with_host:
         e_ms, h2d, d2h = time_e2e(rows, torch, stream, args.e2e_steps)
-        if dist:
-            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": round(bytes_step * ws / (e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+        e_ms = max_over_ranks(e_ms, dist, "cuda")
+        e2e = {"value": round(aggregate_gbs(bytes_step, ws, e_ms), 2), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 3)}
 
     cpu = None
@@ -462,9 +526,11 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "48^4 lattice (5,308,416 sites), every hot-path row A2-A9 once per "
-                                   "step; FP64 rows in the library default arithmetic (df32)",
-                       "lattice": list(DIMS), "layout": "soa",
+            "config": {"workload": ("48^4 lattice (5,308,416 sites), every hot-path row A2-A9 once "
+                                    "per step; FP64 rows in the library default arithmetic (df32)"
+                                    if full else "subset %s on %s" % (args.rows or "all rows",
+                                                                      "x".join(map(str, dims)))),
+                       "lattice": list(dims), "layout": "soa", "pipeline": args.pipeline,
                        "l2": "every field larger than the 129 MB L2; no flush needed",
                        "bytes_per_step": bytes_step, "seed": SEED},
             "sites_per_s": round(a2["Gsites_s"] * 1e9 * ws, 0),

@@ -223,13 +223,32 @@ int su3s_catalogue(char* buf, size_t cap);
 int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int threads,
                     int blocks_per_sm);
 
+/* Choose how FP64-storage kernels move data (process-wide; results do not
+ * depend on it):
+ *   -1  the library's choice per kernel (default);
+ *    0  plain 16-byte vector loads;
+ *    1  TMA-staged tiles: each warp stages its next 32-site tile of every leaf
+ *       with bulk copies into shared memory while it computes the current one;
+ *    2  TMA-staged per leaf: each leaf has its own buffer and barrier, is read
+ *       when first needed and refilled after its last use.
+ * Staging needs 32 sites of a component to be contiguous (SOA, or AOSOA with
+ * block >= 32); otherwise plain loads are used.  EINVAL for other values. */
+int su3s_set_pipeline(int mode);
+
+/* Read and clear the library's device error word (a stream-ordered copy
+ * followed by a synchronisation of `stream`): 0 if every bounded wait inside
+ * the library's kernels completed since the last call, 1 if a TMA pipeline
+ * wait gave up (its results are then incomplete). */
+int su3s_device_error(int* code, void* stream);
+
 /* Autotune the launch geometry for `e` into `dest`: times each candidate
- * (threads 64..512, full or grid-stride grids) with CUDA events on `stream`
- * (synchronising it; dest is overwritten), keeps the fastest for later
- * su3s_eval calls and reports it in *threads / *blocks_per_sm (either may be
- * NULL) and its time in *best_ms (may be NULL). */
+ * (data movement 0/1/2 as for su3s_set_pipeline, threads 64..256, full or
+ * grid-stride grids) with CUDA events on `stream` (synchronising it; dest is
+ * overwritten), keeps the fastest for later su3s_eval calls and reports it in
+ * *threads, *blocks_per_sm, *variant and its time in *best_ms (any may be
+ * NULL). */
 int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream, int* threads,
-              int* blocks_per_sm, float* best_ms);
+              int* blocks_per_sm, int* variant, float* best_ms);
 
 /* ------------------------------------------------------------------------
  * Batching: many (dest, expr) pairs of uneven volumes in one persistent

@@ -84,7 +84,9 @@ def load(build_if_missing=False):
         "su3s_set_default_math": ([I], I),
         "su3s_catalogue": ([ctypes.c_char_p, SZ], I),
         "su3s_set_launch": ([P, P, I, I, I], I),
-        "su3s_tune": ([P, P, I, P, ctypes.POINTER(I), ctypes.POINTER(I),
+        "su3s_set_pipeline": ([I], I),
+        "su3s_device_error": ([ctypes.POINTER(I), P], I),
+        "su3s_tune": ([P, P, I, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                        ctypes.POINTER(ctypes.c_float)], I),
         "su3s_batch_create": ([PP], I),
         "su3s_batch_add": ([P, P, P], I),
@@ -129,6 +131,22 @@ def catalogue():
 
 def set_default_math(math):
     _check(load().su3s_set_default_math(math))
+
+
+PIPE_AUTO, PIPE_PLAIN, PIPE_TMA, PIPE_TMA_LEAF = -1, 0, 1, 2
+
+
+def set_pipeline(mode):
+    """-1 the library's choice, 0 plain loads, 1 TMA-staged tiles, 2 TMA-staged
+    per leaf (FP64 storage; layouts that keep 32 sites contiguous)."""
+    _check(load().su3s_set_pipeline(mode))
+
+
+def device_error(stream=None):
+    """Read and clear the device error word (0 = every bounded wait completed)."""
+    c = ctypes.c_int()
+    _check(load().su3s_device_error(ctypes.byref(c), _stream(stream)))
+    return c.value
 
 
 # ---------------------------------------------------------------- lattice
@@ -357,11 +375,12 @@ def set_launch(dest, expr, threads, blocks_per_sm=0, math=MATH_DEFAULT):
 
 
 def tune(dest, expr, math=MATH_DEFAULT, stream=None):
-    """Autotune the launch geometry; returns (threads, blocks_per_sm, ms)."""
-    t, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    """Autotune data movement and launch geometry; returns
+    (threads, blocks_per_sm, variant, ms)."""
+    t, b, v, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
     _check(_lib.su3s_tune(dest._h, _as_expr(expr)._h, math, _stream(stream), ctypes.byref(t),
-                          ctypes.byref(b), ctypes.byref(ms)))
-    return t.value, b.value, ms.value
+                          ctypes.byref(b), ctypes.byref(v), ctypes.byref(ms)))
+    return t.value, b.value, v.value, ms.value
 
 
 def eval_adjoint(expr, grad_out, grads, math=MATH_DEFAULT, stream=None):

@@ -18,6 +18,23 @@ using namespace su3s;
 
 namespace su3s {
 
+// Device error word: kernels whose bounded pipeline waits give up record a
+// code here; su3s_device_error reads and clears it.
+__device__ int su3s_device_error_flag = 0;
+
+static int* device_error_ptr() {
+  static int* ptr = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, su3s_device_error_flag) == cudaSuccess) ptr = (int*)p;
+  });
+  return ptr;
+}
+
+// -1: choose per launch (TMA-staged where the layout allows), 0: plain loads, 1: TMA-staged
+static int g_pipeline_pref = -1;
+
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
 
@@ -51,13 +68,24 @@ static std::map<std::pair<std::string, int>, EvalEntry>& adj_reg() {
   return m;
 }
 
-void register_eval(const std::string& sig, int prec, int math, LaunchFn fn, const void* kernel,
-                   int vps) {
-  eval_reg()[std::make_tuple(sig, prec, math)] = EvalEntry{fn, kernel, vps};
+static EvalEntry make_entry(const Variants& v, int vps) {
+  EvalEntry e{};
+  for (int i = 0; i < kNumVariants; ++i) {
+    e.fn[i] = v.fn[i];
+    e.kernel[i] = v.kernel[i];
+    e.warp_bytes[i] = v.warp_bytes[i];
+  }
+  e.vps = vps;
+  e.default_variant = v.fn[1] ? v.default_variant : 0;
+  return e;
 }
 
-void register_adjoint(const std::string& sig, int math, LaunchFn fn, const void* kernel) {
-  adj_reg()[std::make_pair(sig, math)] = EvalEntry{fn, kernel, 1};
+void register_eval(const std::string& sig, int prec, int math, const Variants& v, int vps) {
+  eval_reg()[std::make_tuple(sig, prec, math)] = make_entry(v, vps);
+}
+
+void register_adjoint(const std::string& sig, int math, const Variants& v) {
+  adj_reg()[std::make_pair(sig, math)] = make_entry(v, 1);
 }
 
 void ensure_registered() {
@@ -98,23 +126,78 @@ int sm_count() {
 }
 
 struct Geo {
-  int threads, bps;
+  int threads, bps, variant;  // variant -1: automatic
 };
 static std::mutex g_geo_mu;
 static std::map<std::tuple<const void*, int64_t, int>, Geo> g_geo;
 
-void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int bps) {
+void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int bps, int variant) {
   std::lock_guard<std::mutex> lk(g_geo_mu);
-  g_geo[std::make_tuple(kernel, nvec, nmu)] = Geo{threads, bps};
+  g_geo[std::make_tuple(kernel, nvec, nmu)] = Geo{threads, bps, variant};
+}
+
+static bool find_geometry(const void* kernel, int64_t nvec, int nmu, Geo* g) {
+  std::lock_guard<std::mutex> lk(g_geo_mu);
+  auto it = g_geo.find(std::make_tuple(kernel, nvec, nmu));
+  if (it == g_geo.end()) return false;
+  *g = it->second;
+  return true;
+}
+
+bool tma_layout_ok(const su3s_field* f) {
+  return f->layout == SU3S_SOA || f->block >= 32;
+}
+
+// Occupancy of a staged kernel (blocks per SM), cached per (kernel, threads).
+static int staged_occupancy(const void* kernel, int threads, int warp_bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(kernel, threads);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  const size_t smem = (size_t)(threads / 32) * warp_bytes;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * warp_bytes);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1)
+    n = 1;
+  cache[key] = n;
+  return n;
+}
+
+int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* out) {
+  Geo g{0, 0, g_pipeline_pref};
+  find_geometry(e->kernel[0], nvec, nmu, &g);
+  const bool can_stage = e->fn[1] && tma_ok && nvec % 32 == 0;
+  int variant = g.variant;
+  if (variant < 0 || variant >= kNumVariants) variant = e->default_variant;
+  if (!can_stage) variant = 0;
+  if (variant > 0) {
+    int threads = g.threads > 0 ? g.threads : 128;
+    if (variant == 2 && threads > 128) threads = 128;  // per-leaf kernels: at most 4 warps
+    const int occ = staged_occupancy(e->kernel[variant], threads, e->warp_bytes[variant]);
+    const int per_sm = g.bps > 0 && g.bps < occ ? g.bps : occ;
+    const int64_t ntiles = nvec / 32, wpb = threads / 32;
+    int64_t nb = ((int64_t)per_sm * sm_count() + nmu - 1) / nmu;
+    const int64_t need = (ntiles + wpb - 1) / wpb;
+    if (nb > need) nb = need;
+    if (nb < 1) nb = 1;
+    out->fn = e->fn[variant];
+    out->grid = dim3((unsigned)nb, (unsigned)nmu, 1);
+    out->block = dim3((unsigned)threads, 1, 1);
+    out->variant = variant;
+    return SU3S_OK;
+  }
+  out->fn = e->fn[0];
+  out->variant = 0;
+  launch_geometry(e->kernel[0], nvec, nmu, &out->grid, &out->block);
+  return SU3S_OK;
 }
 
 void launch_geometry(const void* kernel, int64_t nvec, int nmu, dim3* grid, dim3* block) {
-  Geo g{256, 0};
-  {
-    std::lock_guard<std::mutex> lk(g_geo_mu);
-    auto it = g_geo.find(std::make_tuple(kernel, nvec, nmu));
-    if (it != g_geo.end()) g = it->second;
-  }
+  Geo g{256, 0, -1};
+  find_geometry(kernel, nvec, nmu, &g);
+  if (g.threads <= 0) g.threads = 256;
   int64_t nb;
   if (g.bps > 0) {
     nb = (int64_t)g.bps * sm_count();
@@ -320,6 +403,7 @@ int build_params(const Canon& c, const su3s_field* dest, int vps, KParams* p) {
   }
   p->nvec = dest->Vpad / vps;
   p->nmu = dest->nmu;
+  p->err = device_error_ptr();
   return SU3S_OK;
 }
 
@@ -362,9 +446,9 @@ static int do_eval(su3s_field* dest, const su3s_expr* e, int math, cudaStream_t 
   }
   KParams p;
   build_params(c, dest, ent->vps, &p);
-  dim3 grid, block;
-  launch_geometry(ent->kernel, p.nvec, p.nmu, &grid, &block);
-  cudaError_t ce = ent->launch(&p, grid, block, st);
+  Launch L;
+  plan_launch(ent, p.nvec, p.nmu, tma_layout_ok(dest), &L);
+  cudaError_t ce = L.fn(&p, L.grid, L.block, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "evaluation kernel launch");
   return ok();
 }
@@ -636,12 +720,13 @@ SU3S_EXPORT int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int 
   if (rc) return rc;
   const EvalEntry* ent = find_eval(c.sig, dest->prec, math_for(dest->prec, math));
   if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s", c.sig.c_str());
-  set_geometry(ent->kernel, dest->Vpad / ent->vps, dest->nmu, threads, blocks_per_sm);
+  set_geometry(ent->kernel[0], dest->Vpad / ent->vps, dest->nmu, threads, blocks_per_sm,
+               g_pipeline_pref);
   return ok();
 }
 
 SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream,
-                          int* threads_out, int* bps_out, float* best_ms) {
+                          int* threads_out, int* bps_out, int* variant_out, float* best_ms) {
   Canon c;
   int rc = check_eval(dest, e, &c);
   if (rc) return rc;
@@ -656,43 +741,66 @@ SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* 
     return fail(SU3S_ECUDA, "event creation failed");
   const int th_c[] = {64, 128, 256};
   const int bps_c[] = {0, 2, 4, 8, 16};
+  const bool tma = ent->fn[1] && tma_layout_ok(dest) && p.nvec % 32 == 0;
   float best = 1e30f;
-  int bt = 256, bb = 0;
-  for (int th : th_c)
-    for (int bps : bps_c) {
-      set_geometry(ent->kernel, p.nvec, p.nmu, th, bps);
-      dim3 grid, block;
-      launch_geometry(ent->kernel, p.nvec, p.nmu, &grid, &block);
-      cudaError_t ce = ent->launch(&p, grid, block, st);  // warm-up
-      if (ce != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cuda_fail(ce, "tuning launch");
+  int bt = 256, bb = 0, bv = 0;
+  for (int var = 0; var < (tma ? kNumVariants : 1); ++var)
+    for (int th : th_c)
+      for (int bps : bps_c) {
+        set_geometry(ent->kernel[0], p.nvec, p.nmu, th, bps, var);
+        Launch L;
+        plan_launch(ent, p.nvec, p.nmu, tma, &L);
+        cudaError_t ce = L.fn(&p, L.grid, L.block, st);  // warm-up
+        if (ce != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return cuda_fail(ce, "tuning launch");
+        }
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) L.fn(&p, L.grid, L.block, st);
+        cudaEventRecord(e1, st);
+        ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return cuda_fail(ce, "tuning run");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        if (ms < best) {
+          best = ms;
+          bt = th;
+          bb = bps;
+          bv = var;
+        }
       }
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < 3; ++r) ent->launch(&p, grid, block, st);
-      cudaEventRecord(e1, st);
-      ce = cudaEventSynchronize(e1);
-      if (ce != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cuda_fail(ce, "tuning run");
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= 3.f;
-      if (ms < best) {
-        best = ms;
-        bt = th;
-        bb = bps;
-      }
-    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_geometry(ent->kernel, p.nvec, p.nmu, bt, bb);
+  set_geometry(ent->kernel[0], p.nvec, p.nmu, bt, bb, bv);
   if (threads_out) *threads_out = bt;
+  if (variant_out) *variant_out = bv;
   if (bps_out) *bps_out = bb;
   if (best_ms) *best_ms = best;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_set_pipeline(int mode) {
+  if (mode < -1 || mode > 2) return fail(SU3S_EINVAL, "pipeline mode must be -1, 0, 1 or 2");
+  g_pipeline_pref = mode;
+  return ok();
+}
+
+SU3S_EXPORT int su3s_device_error(int* code, void* stream) {
+  if (!code) return fail(SU3S_EINVAL, "null argument");
+  int* dev = device_error_ptr();
+  if (!dev) return fail(SU3S_ECUDA, "device error word unavailable");
+  static const int zero = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(code, dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dev, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
   return ok();
 }
 
@@ -729,9 +837,12 @@ SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
   p.gout = gout->desc;
   for (size_t i = 0; i < c.leaves.size(); ++i)
     if (gleaves && gleaves[i]) p.gleaf[i] = gleaves[i]->desc;
-  dim3 grid, block;
-  launch_geometry(ent->kernel, p.k.nvec, p.k.nmu, &grid, &block);
-  cudaError_t ce = ent->launch(&p, grid, block, (cudaStream_t)stream);
+  Launch L;
+  bool tma = tma_layout_ok(gout);
+  for (size_t i = 0; i < c.leaves.size(); ++i)
+    if (gleaves && gleaves[i]) tma = tma && tma_layout_ok(gleaves[i]);
+  plan_launch(ent, p.k.nvec, p.k.nmu, tma, &L);
+  cudaError_t ce = L.fn(&p, L.grid, L.block, (cudaStream_t)stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "adjoint kernel launch");
   return ok();
 }

@@ -181,11 +181,19 @@ struct Operand<Adj<B>> {
   static constexpr bool adj = true;
 };
 
-// Per-site evaluation context: loaded leaves and real factors.
+// Per-site evaluation context: loaded leaves and real factors.  Leaf values
+// are reached through leaf_value<slot, W>() so that a context can also fetch
+// them on demand (the TMA-staged kernels read a leaf from shared memory at its
+// first use and refill its buffer after its last use).
 template <class M, int NL, int NS>
 struct Ctx {
   typename M::R leaf[NL][18];
   typename M::R sc[NS > 0 ? NS : 1];
+  template <int I, int W>
+  __device__ __forceinline__ void leaf_value(typename M::R* out) const {
+#pragma unroll
+    for (int r = 0; r < W; ++r) out[r] = leaf[I][r];
+  }
 };
 
 // ----------------------------------------------------------- primitives
@@ -307,8 +315,7 @@ template <class T, class M, class C>
 __device__ __forceinline__ void value(const C& ctx, typename M::R* out) {
   constexpr int W = Width<T::kind>::value;
   if constexpr (T::is_leaf) {
-#pragma unroll
-    for (int r = 0; r < W; ++r) out[r] = ctx.leaf[T::slot][r];
+    ctx.template leaf_value<T::slot, W>(out);
   } else if constexpr (T::accumulates) {
     typename M::A a[W];
     acc_into<T, M, true, 1>(ctx, a);

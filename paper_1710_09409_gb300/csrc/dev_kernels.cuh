@@ -16,6 +16,7 @@
 
 #include "dev_expr.cuh"
 #include "dev_field.cuh"
+#include "dev_tma.cuh"
 #include "kparams.h"
 
 namespace su3s {
@@ -212,6 +213,456 @@ __global__ void __launch_bounds__(256) k_adjoint(const __grid_constant__ GParams
   }
 }
 
+// ------------------------------------------------- TMA-staged variants
+// FP64 storage.  Each warp owns a 32-site tile buffer in shared memory: it
+// waits for its tile, reads its sites into registers, immediately asks the
+// TMA engine for the next tile (one elected lane issues one bulk copy per leaf
+// component: 32 sites x 16 bytes, contiguous in both layouts when the site
+// block is >= 32), and computes while the copy is in flight.
+
+template <int K, int PREC>
+struct StageBytes {
+  static constexpr int value =
+      K == KR ? 256 : (K == KV ? 3 : (IsC12<PREC>::value ? 6 : 9)) * 512;
+};
+
+template <class Tree, int PREC, int I>
+struct LeafOff {
+  static constexpr int value =
+      LeafOff<Tree, PREC, I - 1>::value + StageBytes<LeafKind<Tree, I - 1>::value, PREC>::value;
+};
+template <class Tree, int PREC>
+struct LeafOff<Tree, PREC, 0> {
+  static constexpr int value = 0;
+};
+
+// bytes of one staged tile: the leaves, plus dL/dZ for reverse mode
+template <class Tree, int PREC, bool GRAD>
+struct TileBytes {
+  static constexpr int value = LeafOff<Tree, PREC, Tree::nleaf>::value +
+                               (GRAD ? StageBytes<Tree::kind, PREC>::value : 0);
+};
+
+// Copies of one tile: every (leaf, component) segment is one bulk copy; the
+// warp's lanes issue them in parallel, lane j taking copy j (and j+32, ...).
+// Copies are numbered leaf by leaf; dL/dZ (reverse mode) comes last.
+template <int K, int PREC>
+struct NCopies {
+  static constexpr int value = K == KR ? 1 : StageBytes<K, PREC>::value / 512;
+};
+
+template <class Tree, int PREC, int I>
+struct CopyBase {
+  static constexpr int value =
+      CopyBase<Tree, PREC, I - 1>::value + NCopies<LeafKind<Tree, I - 1>::value, PREC>::value;
+};
+template <class Tree, int PREC>
+struct CopyBase<Tree, PREC, 0> {
+  static constexpr int value = 0;
+};
+
+// Issue copy number j if it belongs to object (kind K, first copy J0).
+template <int K, int PREC, int J0>
+__device__ __forceinline__ void issue_if_mine(int j, const FieldDesc& f, int64_t s0, int mu,
+                                              unsigned char* dst, uint64_t* bar) {
+  constexpr int N = NCopies<K, PREC>::value;
+  const int c = j - J0;
+  if (c >= 0 && c < N) {
+    const int64_t e = elem_base(f, s0, mu) + (int64_t)c * f.s_c;
+    if constexpr (K == KR) tma_load_1d(dst, (const char*)f.ptr + e * 8, 256, bar);
+    else tma_load_1d(dst + c * 512, (const char*)f.ptr + e * 16, 512, bar);
+  }
+}
+
+template <class Tree, int I, int PREC>
+__device__ __forceinline__ void issue_leaves_j(int j, const KParams& p, int64_t s0, int mu,
+                                               unsigned char* buf, uint64_t* bar) {
+  if constexpr (I < Tree::nleaf) {
+    issue_if_mine<LeafKind<Tree, I>::value, PREC, CopyBase<Tree, PREC, I>::value>(
+        j, p.leaf[I], s0, mu, buf + LeafOff<Tree, PREC, I>::value, bar);
+    issue_leaves_j<Tree, I + 1, PREC>(j, p, s0, mu, buf, bar);
+  }
+}
+
+// Whole warp: expect the tile's bytes (lane 0), then issue its copies.
+template <class Tree, int PREC, bool GRAD>
+__device__ __forceinline__ void issue_tile(int lane, const KParams& p, const FieldDesc* gout,
+                                           int64_t s0, int mu, unsigned char* buf, uint64_t* bar) {
+  constexpr int NL = Tree::nleaf;
+  constexpr int NJ = CopyBase<Tree, PREC, NL>::value + (GRAD ? NCopies<Tree::kind, PREC>::value : 0);
+  if (lane == 0) mbar_arrive_expect_tx(bar, TileBytes<Tree, PREC, GRAD>::value);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < (NJ + 31) / 32; ++r) {
+    const int j = lane + 32 * r;
+    issue_leaves_j<Tree, 0, PREC>(j, p, s0, mu, buf, bar);
+    if constexpr (GRAD)
+      issue_if_mine<Tree::kind, PREC, CopyBase<Tree, PREC, NL>::value>(
+          j, *gout, s0, mu, buf + LeafOff<Tree, PREC, NL>::value, bar);
+  }
+}
+
+// Read this lane's site of a staged object into ctx.leaf[slot].
+template <int K, int PREC, class M, class C>
+__device__ __forceinline__ void read_obj(const unsigned char* src, int lane, C& ctx, int slot) {
+  if constexpr (K == KR) {
+    const uint2 v = reinterpret_cast<const uint2*>(src)[lane];
+    if constexpr (M::kNative64) ctx.leaf[slot][0] = u2d(v.x, v.y);
+    else ctx.leaf[slot][0] = df_split_bits(v.x, v.y);
+  } else {
+    constexpr int NC = StageBytes<K, PREC>::value / 512;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const uint4 v = reinterpret_cast<const uint4*>(src + c * 512)[lane];
+      if constexpr (M::kNative64) {
+        ctx.leaf[slot][2 * c] = u2d(v.x, v.y);
+        ctx.leaf[slot][2 * c + 1] = u2d(v.z, v.w);
+      } else {
+        ctx.leaf[slot][2 * c] = df_split_bits(v.x, v.y);
+        ctx.leaf[slot][2 * c + 1] = df_split_bits(v.z, v.w);
+      }
+    }
+    if constexpr (K == KM && IsC12<PREC>::value) rebuild_row2<M>(ctx.leaf[slot]);
+  }
+}
+
+template <class Tree, int I, int PREC, class M, class C>
+__device__ __forceinline__ void read_leaves(const unsigned char* buf, int lane, C& ctx) {
+  if constexpr (I < Tree::nleaf) {
+    read_obj<LeafKind<Tree, I>::value, PREC, M>(buf + LeafOff<Tree, PREC, I>::value, lane, ctx, I);
+    read_leaves<Tree, I + 1, PREC, M>(buf, lane, ctx);
+  }
+}
+
+template <class Tree, class M, int PREC>
+__global__ void __launch_bounds__(256) k_eval_tma(const __grid_constant__ KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NL = Tree::nleaf;
+  constexpr int NS = Tree::nsc;
+  constexpr int W = Width<Tree::kind>::value;
+  constexpr int TB = TileBytes<Tree, PREC, false>::value;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  unsigned char* buf = smem + warp * (TB + 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf + TB);
+  const int mu = blockIdx.y;
+  const int64_t ntiles = p.nvec >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * nwarps;
+  int64_t t = (int64_t)blockIdx.x * nwarps + warp;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  if (t < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, t << 5, mu, buf, bar);
+  Ctx<M, NL, NS> ctx;
+#pragma unroll
+  for (int k = 0; k < (NS > 0 ? NS : 1); ++k) ctx.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
+  uint32_t phase = 0;
+  while (t < ntiles) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase));
+    if (!ok) {
+      if (lane == 0) report_timeout(p.err, bar, phase);
+      break;
+    }
+    phase ^= 1;
+    read_leaves<Tree, 0, PREC, M>(buf, lane, ctx);
+    fence_proxy_async_smem();
+    __syncwarp();
+    const int64_t tn = t + wstride;
+    if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, tn << 5, mu, buf, bar);
+    typename M::A acc[1][W];
+    if constexpr (Tree::accumulates) {
+      acc_into<Tree, M, true, 1>(ctx, acc[0]);
+    } else {
+      typename M::R val[W];
+      value<Tree, M>(ctx, val);
+#pragma unroll
+      for (int r = 0; r < W; ++r) acc[0][r] = M::to_acc(val[r]);
+    }
+    store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + lane, mu, acc);
+    t = tn;
+  }
+}
+
+template <class Tree, class M>
+__global__ void __launch_bounds__(256) k_adjoint_tma(const __grid_constant__ GParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NL = Tree::nleaf;
+  constexpr int NS = Tree::nsc;
+  constexpr int TB = TileBytes<Tree, P_F64, true>::value;
+  constexpr int GOFF = LeafOff<Tree, P_F64, NL>::value;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  unsigned char* buf = smem + warp * (TB + 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf + TB);
+  const int mu = blockIdx.y;
+  const int64_t ntiles = p.k.nvec >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * nwarps;
+  int64_t t = (int64_t)blockIdx.x * nwarps + warp;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  if (t < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, t << 5, mu, buf, bar);
+  Ctx<M, NL, NS> ctx;
+#pragma unroll
+  for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
+    ctx.sc[k] = M::scalar(p.k.sc[k], p.k.sch[k], p.k.scl[k]);
+  uint32_t phase = 0;
+  while (t < ntiles) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase));
+    if (!ok) {
+      if (lane == 0) report_timeout(p.k.err, bar, phase);
+      break;
+    }
+    phase ^= 1;
+    read_leaves<Tree, 0, P_F64, M>(buf, lane, ctx);
+    Ctx<M, 1, 0> g;
+    read_obj<Tree::kind, P_F64, M>(buf + GOFF, lane, g, 0);
+    fence_proxy_async_smem();
+    __syncwarp();
+    const int64_t tn = t + wstride;
+    if (tn < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, tn << 5, mu, buf, bar);
+    GradAcc<M, NL> ga;
+#pragma unroll
+    for (int i = 0; i < NL; ++i)
+#pragma unroll
+      for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
+    GradSink<Tree, M> sink{&p, (t << 5) + lane, mu};
+    Rev<Tree>::template run<Tree, M>(ctx, g.leaf[0], ga, sink);
+    store_repeated<Tree, 0, M>(ga, sink);
+    t = tn;
+  }
+}
+
+// ------------------------------------------- lazily staged (per-leaf) variant
+// Each leaf has its own buffer and mbarrier per warp.  A leaf is read from
+// shared memory when the evaluator first needs it; a leaf used once has its
+// buffer refilled with the next tile right after that read, a leaf used more
+// than once after the tile is computed.  Register pressure follows the
+// evaluation order (as with plain loads) while copies overlap compute.
+// Times leaf slot I is read from its buffer per tile: once per occurrence in
+// forward evaluation; in reverse mode a product also re-reads the leaves of a
+// composite operand when it back-propagates into it.
+template <class T, int I>
+struct RevReads {
+  static constexpr int value = 0;
+};
+template <class X, class Y, int I>
+struct RevReads<Mul<X, Y>, I> {
+  using BX = typename Operand<X>::base;
+  using BY = typename Operand<Y>::base;
+  static constexpr int value =
+      Count<BX, I>::value + Count<BY, I>::value + RevReads<BX, I>::value + RevReads<BY, I>::value;
+};
+template <class X, class Y, int I>
+struct RevReads<Add<X, Y>, I> {
+  static constexpr int value = RevReads<X, I>::value + RevReads<Y, I>::value;
+};
+template <class X, class Y, int I>
+struct RevReads<Sub<X, Y>, I> {
+  static constexpr int value = RevReads<X, I>::value + RevReads<Y, I>::value;
+};
+template <int K, class X, int I>
+struct RevReads<Scale<K, X>, I> {
+  static constexpr int value = RevReads<X, I>::value;
+};
+template <class X, int I>
+struct RevReads<Adj<X>, I> {
+  static constexpr int value = RevReads<X, I>::value;
+};
+template <class Tree, int I, bool GRAD>
+struct Reads {
+  static constexpr int value =
+      GRAD ? (Tree::is_leaf ? Count<Tree, I>::value : RevReads<Tree, I>::value) : Count<Tree, I>::value;
+};
+
+template <class Tree, int PREC, bool GRAD>
+struct LazyLayout {
+  static constexpr int NL = Tree::nleaf;
+  static constexpr int NB = NL + (GRAD ? 1 : 0);   // barriers
+  static constexpr int DATA = TileBytes<Tree, PREC, GRAD>::value;
+  static constexpr int BYTES = DATA + 8 * NB;      // + one barrier per buffer
+  static constexpr int STRIDE = (BYTES + 15) / 16 * 16;
+};
+
+template <class Tree, class M, int PREC, bool GRAD>
+struct LazyCtx {
+  using L = LazyLayout<Tree, PREC, GRAD>;
+  static constexpr int NL = Tree::nleaf;
+  static constexpr int NS = Tree::nsc;
+  unsigned char* buf;
+  uint64_t* bars;
+  const KParams* p;
+  const FieldDesc* gout;
+  int64_t next_s0;
+  int mu, lane;
+  uint32_t parity;
+  bool has_next;
+  mutable bool dead;
+  typename M::R sc[NS > 0 ? NS : 1];
+
+  template <int I>
+  __device__ __forceinline__ void issue(int64_t s0) const {
+    constexpr int K = I < NL ? LeafKind<Tree, I>::value : Tree::kind;
+    constexpr int OFF = LeafOff<Tree, PREC, I>::value;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[I], StageBytes<K, PREC>::value);
+    __syncwarp();
+    const FieldDesc& f = I < NL ? p->leaf[I < NL ? I : 0] : *gout;
+    issue_if_mine<K, PREC, 0>(lane, f, s0, mu, buf + OFF, &bars[I]);
+  }
+
+  // wait for leaf I of the current tile (bounded; a time-out marks the warp dead)
+  template <int I>
+  __device__ __forceinline__ void wait_leaf() const {
+    if (dead) return;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[I], parity));
+    if (!ok) {
+      if (lane == 0 && p->err) atomicExch(p->err, kErrTmaTimeout);
+      dead = true;
+    }
+  }
+
+  template <int I, int W>
+  __device__ __forceinline__ void leaf_value(typename M::R* out) const {
+    constexpr int K = I < NL ? LeafKind<Tree, I>::value : Tree::kind;
+    wait_leaf<I>();
+    Ctx<M, 1, 0> tmp;
+    read_obj<K, PREC, M>(buf + LeafOff<Tree, PREC, I>::value, lane, tmp, 0);
+#pragma unroll
+    for (int r = 0; r < W; ++r) out[r] = tmp.leaf[0][r];
+    if constexpr (I >= NL || Reads<Tree, (I < NL ? I : 0), GRAD>::value == 1) {
+      // single use: hand the buffer back for the next tile now
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (has_next && !dead) issue<I>(next_s0);
+    }
+  }
+
+  // after the tile: refill leaves used more than once
+  template <int I>
+  __device__ __forceinline__ void refill_repeated() const {
+    if constexpr (I < NL) {
+      if constexpr (Reads<Tree, I, GRAD>::value != 1) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (has_next && !dead) issue<I>(next_s0);
+      }
+      refill_repeated<I + 1>();
+    }
+  }
+
+  template <int I>
+  __device__ __forceinline__ void issue_all(int64_t s0) const {
+    if constexpr (I < L::NB) {
+      issue<I>(s0);
+      issue_all<I + 1>(s0);
+    }
+  }
+
+  // after a time-out: let copies in flight land (bounded), once per barrier
+  template <int I>
+  __device__ __forceinline__ void drain() const {
+    if constexpr (I < L::NB) {
+      mbar_wait_bounded(&bars[I], parity);
+      drain<I + 1>();
+    }
+  }
+};
+
+template <class Tree, class M, int PREC, bool GRAD>
+__device__ __forceinline__ void lazy_setup(LazyCtx<Tree, M, PREC, GRAD>& c, unsigned char* smem,
+                                           const KParams& p, const FieldDesc* gout) {
+  using L = LazyLayout<Tree, PREC, GRAD>;
+  const int warp = threadIdx.x >> 5;
+  c.lane = threadIdx.x & 31;
+  c.buf = smem + warp * L::STRIDE;
+  c.bars = reinterpret_cast<uint64_t*>(c.buf + L::DATA);
+  c.p = &p;
+  c.gout = gout;
+  c.mu = blockIdx.y;
+  c.parity = 0;
+  c.dead = false;
+  if (c.lane == 0) {
+#pragma unroll
+    for (int i = 0; i < L::NB; ++i) mbar_init(&c.bars[i], 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < (Tree::nsc > 0 ? Tree::nsc : 1); ++k)
+    c.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
+}
+
+template <class Tree, class M, int PREC>
+__global__ void __launch_bounds__(128, 4) k_eval_lazy(const __grid_constant__ KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int W = Width<Tree::kind>::value;
+  LazyCtx<Tree, M, PREC, false> c;
+  lazy_setup(c, smem, p, nullptr);
+  const int nwarps = blockDim.x >> 5;
+  const int64_t ntiles = p.nvec >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * nwarps;
+  int64_t t = (int64_t)blockIdx.x * nwarps + (threadIdx.x >> 5);
+  if (t < ntiles) c.template issue_all<0>(t << 5);
+  while (t < ntiles) {
+    const int64_t tn = t + wstride;
+    c.has_next = tn < ntiles;
+    c.next_s0 = tn << 5;
+    typename M::A acc[1][W];
+    if constexpr (Tree::accumulates) {
+      acc_into<Tree, M, true, 1>(c, acc[0]);
+    } else {
+      typename M::R val[W];
+      value<Tree, M>(c, val);
+#pragma unroll
+      for (int r = 0; r < W; ++r) acc[0][r] = M::to_acc(val[r]);
+    }
+    c.template refill_repeated<0>();
+    if (c.dead) break;
+    store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
+    c.parity ^= 1;
+    t = tn;
+  }
+  if (c.dead) c.template drain<0>();
+}
+
+template <class Tree, class M>
+__global__ void __launch_bounds__(128, 4) k_adjoint_lazy(const __grid_constant__ GParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NL = Tree::nleaf;
+  constexpr int W = Width<Tree::kind>::value;
+  LazyCtx<Tree, M, P_F64, true> c;
+  lazy_setup(c, smem, p.k, &p.gout);
+  const int nwarps = blockDim.x >> 5;
+  const int64_t ntiles = p.k.nvec >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * nwarps;
+  int64_t t = (int64_t)blockIdx.x * nwarps + (threadIdx.x >> 5);
+  if (t < ntiles) c.template issue_all<0>(t << 5);
+  while (t < ntiles) {
+    const int64_t tn = t + wstride;
+    c.has_next = tn < ntiles;
+    c.next_s0 = tn << 5;
+    typename M::R G[W];
+    c.template leaf_value<NL, W>(G);   // dL/dZ
+    GradAcc<M, NL> ga;
+#pragma unroll
+    for (int i = 0; i < NL; ++i)
+#pragma unroll
+      for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
+    GradSink<Tree, M> sink{&p, (t << 5) + c.lane, c.mu};
+    Rev<Tree>::template run<Tree, M>(c, G, ga, sink);
+    store_repeated<Tree, 0, M>(ga, sink);
+    c.template refill_repeated<0>();
+    if (c.dead) break;
+    c.parity ^= 1;
+    t = tn;
+  }
+  if (c.dead) c.template drain<0>();
+}
+
 // ------------------------------------------------------------ launchers
 using LaunchFn = cudaError_t (*)(const void* params, dim3 grid, dim3 block, cudaStream_t st);
 
@@ -224,6 +675,68 @@ cudaError_t launch_eval(const void* params, dim3 grid, dim3 block, cudaStream_t 
 template <class Tree, class M>
 cudaError_t launch_adjoint(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
   k_adjoint<Tree, M><<<grid, block, 0, st>>>(*static_cast<const GParams*>(params));
+  return cudaGetLastError();
+}
+
+// Dynamic shared memory of a TMA-staged launch: one tile buffer and one
+// barrier per warp.
+inline size_t tma_smem(int tile_bytes, dim3 block) { return (size_t)(block.x / 32) * (tile_bytes + 16); }
+
+template <class Tree, class M, int PREC>
+cudaError_t launch_eval_tma(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int TB = TileBytes<Tree, PREC, false>::value;
+  const size_t sm = tma_smem(TB, block);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_eval_tma<Tree, M, PREC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * (TB + 16));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_eval_tma<Tree, M, PREC><<<grid, block, sm, st>>>(*static_cast<const KParams*>(params));
+  return cudaGetLastError();
+}
+
+template <class Tree, class M>
+cudaError_t launch_adjoint_tma(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int TB = TileBytes<Tree, P_F64, true>::value;
+  const size_t sm = tma_smem(TB, block);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_tma<Tree, M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * (TB + 16));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_adjoint_tma<Tree, M><<<grid, block, sm, st>>>(*static_cast<const GParams*>(params));
+  return cudaGetLastError();
+}
+
+template <class Tree, class M, int PREC>
+cudaError_t launch_eval_lazy(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int S = LazyLayout<Tree, PREC, false>::STRIDE;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_eval_lazy<Tree, M, PREC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * S);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_eval_lazy<Tree, M, PREC><<<grid, block, (block.x / 32) * S, st>>>(*static_cast<const KParams*>(params));
+  return cudaGetLastError();
+}
+
+template <class Tree, class M>
+cudaError_t launch_adjoint_lazy(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int S = LazyLayout<Tree, P_F64, true>::STRIDE;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_lazy<Tree, M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * S);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_adjoint_lazy<Tree, M><<<grid, block, (block.x / 32) * S, st>>>(*static_cast<const GParams*>(params));
   return cudaGetLastError();
 }
 
@@ -265,21 +778,95 @@ struct Sig<Adj<X>> {
   static std::string str() { return "adj(" + Sig<X>::str() + ")"; }
 };
 
-// Registry hooks implemented by the library (api.cu).
-void register_eval(const std::string& sig, int prec, int math, LaunchFn fn, const void* kernel,
-                   int vps);
-void register_adjoint(const std::string& sig, int math, LaunchFn fn, const void* kernel);
+// Registry hooks implemented by the library (api.cu).  A TMA-staged variant
+// (null for reduced-precision storage) is registered beside the plain one,
+// with its tile bytes per warp.
+// Default data movement of a tree (measured on the GB300 at 48^4, FP64
+// storage, pair arithmetic): trees that read a leaf twice or nest products are
+// issue-bound and keep plain loads; trees of at most two leaves stage whole
+// tiles; sums of products of distinct leaves stage leaf by leaf.  Reverse
+// mode stages whole tiles for products and sums of products.
+template <class T, int I>
+struct AnyRepeat {
+  static constexpr bool value = Count<T, I>::value > 1 || AnyRepeat<T, I - 1>::value;
+};
+template <class T>
+struct AnyRepeat<T, -1> {
+  static constexpr bool value = false;
+};
+template <class T>
+struct IsProd {
+  static constexpr bool value = false;
+};
+template <class X, class Y>
+struct IsProd<Mul<X, Y>> {
+  static constexpr bool value = Operand<X>::base::is_leaf && Operand<Y>::base::is_leaf;
+};
+template <int K, class X>
+struct IsProd<Scale<K, X>> {
+  static constexpr bool value = IsProd<X>::value;
+};
+template <class T>
+struct IsSumOfProds {
+  static constexpr bool value = false;
+};
+template <class X, class Y>
+struct IsSumOfProds<Add<X, Y>> {
+  static constexpr bool value = IsProd<X>::value && IsProd<Y>::value;
+};
+template <class X, class Y>
+struct IsSumOfProds<Sub<X, Y>> {
+  static constexpr bool value = IsProd<X>::value && IsProd<Y>::value;
+};
+template <class Tree, bool GRAD>
+constexpr int default_variant() {
+  if (AnyRepeat<Tree, Tree::nleaf - 1>::value) return 0;
+  if (Tree::nleaf <= 2) return 1;
+  if (IsSumOfProds<Tree>::value) return GRAD ? 1 : 2;
+  return 0;
+}
+
+// Kernel variants of one tree: plain loads, TMA-staged eagerly (whole tile),
+// TMA-staged lazily (per leaf).  The staged variants exist for FP64 storage.
+struct Variants {
+  LaunchFn fn[3];
+  const void* kernel[3];
+  int warp_bytes[3];  // shared memory per warp (0 for plain loads)
+  int default_variant;
+};
+void register_eval(const std::string& sig, int prec, int math, const Variants& v, int vps);
+void register_adjoint(const std::string& sig, int math, const Variants& v);
 
 template <class Tree, class M, int PREC>
 void reg_eval(int math) {
-  register_eval(Sig<Tree>::str(), PREC, math, &launch_eval<Tree, M, PREC>,
-                (const void*)&k_eval<Tree, M, PREC>, Vps<PREC>::value);
+  Variants v{};
+  v.fn[0] = &launch_eval<Tree, M, PREC>;
+  v.kernel[0] = (const void*)&k_eval<Tree, M, PREC>;
+  if constexpr (PREC == P_F64 || PREC == P_F64_C12) {
+    v.fn[1] = &launch_eval_tma<Tree, M, PREC>;
+    v.kernel[1] = (const void*)&k_eval_tma<Tree, M, PREC>;
+    v.warp_bytes[1] = TileBytes<Tree, PREC, false>::value + 16;
+    v.fn[2] = &launch_eval_lazy<Tree, M, PREC>;
+    v.kernel[2] = (const void*)&k_eval_lazy<Tree, M, PREC>;
+    v.warp_bytes[2] = LazyLayout<Tree, PREC, false>::STRIDE;
+    v.default_variant = default_variant<Tree, false>();
+  }
+  register_eval(Sig<Tree>::str(), PREC, math, v, Vps<PREC>::value);
 }
 
 template <class Tree, class M>
 void reg_adjoint(int math) {
-  register_adjoint(Sig<Tree>::str(), math, &launch_adjoint<Tree, M>,
-                   (const void*)&k_adjoint<Tree, M>);
+  Variants v{};
+  v.fn[0] = &launch_adjoint<Tree, M>;
+  v.kernel[0] = (const void*)&k_adjoint<Tree, M>;
+  v.fn[1] = &launch_adjoint_tma<Tree, M>;
+  v.kernel[1] = (const void*)&k_adjoint_tma<Tree, M>;
+  v.warp_bytes[1] = TileBytes<Tree, P_F64, true>::value + 16;
+  v.fn[2] = &launch_adjoint_lazy<Tree, M>;
+  v.kernel[2] = (const void*)&k_adjoint_lazy<Tree, M>;
+  v.warp_bytes[2] = LazyLayout<Tree, P_F64, true>::STRIDE;
+  v.default_variant = default_variant<Tree, true>();
+  register_adjoint(Sig<Tree>::str(), math, v);
 }
 
 // ------------------------------------------------------------ catalogue

@@ -40,9 +40,8 @@ struct df {
 
 // FP64 bit pattern (lo32, hi32) -> (xh, xl).  No FP64 instruction.
 __device__ __forceinline__ df df_split_bits(uint32_t lo32, uint32_t hi32) {
-  uint32_t u = hi32 & 0x7FFFFFFFu;
-  u = max(u, 0x38000000u);                   // exponents below 2^-126 collapse to 0
-  uint32_t w = u - 0x38000000u;              // rebias 1023 -> 127
+  // rebias 1023 -> 127; exponents below 2^-126 collapse to 0 (fused add + max)
+  const uint32_t w = (uint32_t)__viaddmax_s32((int)(hi32 & 0x7FFFFFFFu), -0x38000000, 0);
   uint32_t t = __funnelshift_l(lo32, w, 3);  // exponent + top 23 fraction bits
   uint32_t hb = t | (hi32 & 0x80000000u);
   float xh = __uint_as_float(hb);
@@ -67,7 +66,7 @@ __device__ __forceinline__ double df_to_double(float S, float lo) {
   uint32_t low29 = min(__float2uint_rz(__fmul_rn(fabsf(e), pw)), 0x1FFFFFFFu);
   uint32_t hiw = ((fa >> 3) + 0x38000000u) | sg;
   hiw = fa ? hiw : sg;
-  uint32_t low = fa ? ((fs << 29) | low29) : 0u;
+  uint32_t low = fs * 0x20000000u + low29;  // (fs << 29) | low29; both zero when s == 0
   return __hiloint2double((int)hiw, (int)low);
 }
 

@@ -58,10 +58,21 @@ int check_same_shape(const su3s_field* a, const su3s_field* b, bool same_prec);
 int sm_count();
 
 // kernel registry
+// Variants: 0 plain loads, 1 TMA-staged whole tile, 2 TMA-staged per leaf.
+constexpr int kNumVariants = 3;
 struct EvalEntry {
-  cudaError_t (*launch)(const void*, dim3, dim3, cudaStream_t);
-  const void* kernel;
+  cudaError_t (*fn[kNumVariants])(const void*, dim3, dim3, cudaStream_t);
+  const void* kernel[kNumVariants];
+  int warp_bytes[kNumVariants];  // shared memory per warp of the staged variants
   int vps;
+  int default_variant;           // chosen when no geometry is set
+};
+
+// A resolved launch: which variant, and its geometry.
+struct Launch {
+  cudaError_t (*fn)(const void*, dim3, dim3, cudaStream_t);
+  dim3 grid, block;
+  int variant;
 };
 
 const EvalEntry* find_eval(const std::string& sig, int prec, int math);
@@ -70,7 +81,11 @@ void ensure_registered();
 
 // launch geometry (tuned or default) for a kernel over nvec site vectors
 void launch_geometry(const void* kernel, int64_t nvec, int nmu, dim3* grid, dim3* block);
-void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int blocks_per_sm);
+void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int blocks_per_sm,
+                  int variant = -1);
+// resolve variant + geometry for an entry; tma_ok: the fields allow 32-site tiles
+int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* out);
+bool tma_layout_ok(const su3s_field* f);
 
 // fill a KParams from a canonical tree and destination
 int build_params(const Canon& c, const su3s_field* dest, int vps, KParams* p);

@@ -32,6 +32,7 @@ struct KParams {
   float scl[kMaxScalars];
   int64_t nvec;             // site vectors per link (= Vpad / sites per vector)
   int32_t nmu;
+  int* err;                 // device error word (bounded waits that gave up), may be null
 };
 
 // Adjoint kernels: leaf fields are read, grad_out is read, leaf gradients

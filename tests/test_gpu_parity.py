@@ -479,6 +479,47 @@ def test_batch_matches_separate_evaluations(su3s, math):
     assert sites > 0 and tiles > 0
 
 
+# --------------------------------------------- staged vs plain data movement
+@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2], LAYOUTS[3]], ids=layout_id)
+def test_tma_staging_is_bitwise_identical(su3s, lay, math):
+    """The TMA-staged kernels (bulk copies into shared memory, one 32-site tile
+    per warp) and the plain-load kernels run the same arithmetic per site."""
+    dims = (8, 8, 8, 9)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, nmu=4, names=("a", "b", "c", "d", "w"))
+    F = {n: upload(su3s, lat, f[n], nmu=4, layout=lay[1], block=lay[2]) for n in "abcdw"}
+    a, b, c, d = (F[n] for n in "abcd")
+    exprs = [a * b, a * b + c * d, a.adj() * b - b * a.adj(), a * b * c + 0.5 * d]
+    try:
+        for e in exprs:
+            outs = []
+            for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF):
+                su3s.set_pipeline(mode)
+                z = a.like()
+                su3s.evaluate(z, e, math)
+                outs.append(z.download())
+            assert np.array_equal(outs[0], outs[1])
+            assert np.array_equal(outs[0], outs[2])
+        grads = []
+        for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF):
+            su3s.set_pipeline(mode)
+            g = [a.like() for _ in range(4)]
+            su3s.eval_adjoint(a * b + c * d, F["w"], g, math)
+            g2 = [a.like() for _ in range(4)]
+            su3s.eval_adjoint(a * b * c + 0.5 * d, F["w"], g2, math)
+            grads.append([x.download() for x in g + g2])
+        for x, y, w in zip(*grads):
+            assert np.array_equal(x, y) and np.array_equal(x, w)
+    finally:
+        su3s.set_pipeline(su3s.PIPE_AUTO)
+    assert su3s.device_error() == 0
+    ref = oracle.eval_tree(E1, f)
+    z = a.like()
+    su3s.evaluate(z, a * b + c * d, math)
+    assert np.abs(z.download() - ref).max() < 2 * TOL
+
+
 # ---------------------------------------------------------- tuning
 def test_launch_geometry_does_not_change_results(su3s):
     dims = (8, 8, 8, 8)
@@ -497,9 +538,10 @@ def test_launch_geometry_does_not_change_results(su3s):
             if ref is None:
                 ref = got
             assert np.array_equal(got, ref)
-        th, bps, ms = su3s.tune(z, e, math)
+        th, bps, var, ms = su3s.tune(z, e, math)
         su3s.evaluate(z, e, math)
         assert np.array_equal(z.download(), ref) and th in (64, 128, 256) and ms > 0
+        assert var in (0, 1, 2)
         outs.append(ref)
 
 
