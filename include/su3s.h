@@ -152,6 +152,29 @@ int su3s_field_upload(su3s_field* f, const double* host_canonical, size_t n_doub
 int su3s_field_download(const su3s_field* f, double* host_canonical, size_t n_doubles,
                         void* stream);
 
+/* Download without allocating device memory (the paper has no counterpart:
+ * this is a service of the library).  Same result as su3s_field_download, but
+ * the unpack kernel stages the canonical array in a fixed 16 MiB array in the
+ * library's own device memory instead of a buffer allocated for the call.  It
+ * is meant for callers that cannot allocate device memory at that point: a
+ * framework whose caching allocator already holds the device's memory, or
+ * code that must not pay the latency or implicit synchronisation of
+ * allocating and freeing.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).
+ *   - Limit: V*nmu*w <= 2^21 doubles (16 MiB, e.g. a 16^4 matrix field, an
+ *     8^4 Lorentz field); larger fields return ESHAPE with a message pointing
+ *     to su3s_field_download.
+ *   - The staging array is held by every GPU on which the library is used
+ *     until the process exits.  Its device address is looked up on the first
+ *     call made on each device (with that device current); make that first
+ *     call before any stream capture.
+ *   - Every call shares the array and it keeps the last call's contents; calls
+ *     whose work overlaps on the GPU (other streams, other threads) race on it.
+ *     Calls ordered on one stream do not.
+ * The data is in host_canonical once the stream reaches this point. */
+int su3s_field_download_static(const su3s_field* f, double* host_canonical, size_t n_doubles,
+                               void* stream);
+
 /* ------------------------------------------------------------------------
  * Expressions (Sec. 3, Listing 1: the expression-template tree)
  * ---------------------------------------------------------------------- */

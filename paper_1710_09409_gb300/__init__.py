@@ -70,6 +70,7 @@ def load(build_if_missing=False):
         "su3s_field_unpack": ([P, P, P], I),
         "su3s_field_upload": ([P, P, SZ, P], I),
         "su3s_field_download": ([P, P, SZ, P], I),
+        "su3s_field_download_static": ([P, P, SZ, P], I),
         "su3s_expr_leaf": ([P, PP], I),
         "su3s_expr_mul": ([P, P, PP], I),
         "su3s_expr_add": ([P, P, PP], I),
@@ -245,6 +246,17 @@ class Field:
         _check(_lib.su3s_field_download(self._h, ctypes.c_void_p(out.data_ptr()), out.numel(),
                                         _stream(stream)))
         return out
+
+    def download_static(self, stream=None):
+        """Canonical float64 copy on the host through the library's fixed
+        staging array: no device memory is allocated (fields up to 2^21
+        doubles; synchronous)."""
+        import torch
+        res = np.empty(self.canonical_shape, dtype=np.float64)
+        _check(_lib.su3s_field_download_static(self._h, ctypes.c_void_p(res.ctypes.data), res.size,
+                                               _stream(stream)))
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        return res
 
     def pack(self, dev_canonical, stream=None):
         """Fill the field from a canonical float64 CUDA tensor."""
