@@ -327,22 +327,59 @@ def time_step(rows, torch, stream, steps, warmup, per_row_events=True):
 
 
 def time_e2e(rows, torch, stream, steps):
+    """The step through the C ABI from pinned host buffers.  Every distinct
+    input field is uploaded (H2D copy + pack kernel) once per step on an upload
+    stream, each row runs on the compute stream as soon as its inputs are in,
+    and its outputs are unpacked and copied back on a download stream; events
+    order the three, so host->device copies, kernels and device->host copies
+    of different rows overlap.  Returns (ms per step, H2D bytes, D2H bytes)."""
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    comp = stream
+    fields, order = {}, []
+    for r in rows:
+        for f, h in r.inputs:
+            if id(f) not in fields:
+                fields[id(f)] = (f, h)
+                order.append(id(f))
+    last_use = {}
+
     def one():
+        ready = {}
+        for fid in order:
+            f, h = fields[fid]
+            if fid in last_use:                 # previous step's readers are done with f
+                up.wait_event(last_use[fid])
+            f.upload(h, up)
+            ev = torch.cuda.Event()
+            ev.record(up)
+            ready[fid] = ev
         for r in rows:
-            for f, h in r.inputs:
-                f.upload(h, stream)
-            r.run(stream)
+            for f, _ in r.inputs:
+                comp.wait_event(ready[id(f)])
+            r.run(comp)
+            done = torch.cuda.Event()
+            done.record(comp)
+            for f, _ in r.inputs:
+                last_use[id(f)] = done
+            down.wait_event(done)
             for f, h in r.outputs:
-                f.download(out=h, stream=stream)
+                f.download(out=h, stream=down)
+        fin = torch.cuda.Event()
+        fin.record(down)
+        comp.wait_event(fin)                    # outputs reused next step only after download
+
     one()
-    stream.synchronize()
+    torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    start.record(stream)
+    start.record(comp)
+    up.wait_stream(comp)
+    down.wait_stream(comp)
     for _ in range(steps):
         one()
-    end.record(stream)
+    end.record(comp)
     end.synchronize()
-    h2d = sum(h.numel() * 8 for r in rows for _, h in r.inputs)
+    torch.cuda.synchronize()
+    h2d = sum(fields[fid][1].numel() * 8 for fid in order)
     d2h = sum(h.numel() * 8 for r in rows for _, h in r.outputs)
     return start.elapsed_time(end) / steps, h2d, d2h
 
@@ -398,6 +435,194 @@ def cpu_oracle_sample(budget_s=12.0, frac_sites=1 << 16):
             "seconds": el, "passes": reps, "bytes_per_pass": bytes_one}
 
 
+# ----------------------------------------------------------------- studies
+def _time_ms(torch, stream, fn, reps=20, warm=3):
+    for _ in range(warm):
+        fn()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    s0.record(stream)
+    for _ in range(reps):
+        fn()
+    s1.record(stream)
+    s1.synchronize()
+    return s0.elapsed_time(s1) / reps
+
+
+def run_studies(su3s, synth, torch, stream, which):
+    """Measurements the configurations ask for beside the step, one JSON line
+    each: the L^4 volume sweep (A2-A4), fused vs term-by-term trees (32^4),
+    reduced-precision and two-row errors against the FP64 oracle (32^4 and
+    16^3x32), batched graph vs separate launches (64 lattices), and the layout /
+    site-block sweep of z=a*b (the vector-length study of Sec. 5, Fig. 4)."""
+    import oracle
+    out = []
+    F64, MAT, VEC = su3s.F64, su3s.MATRIX, su3s.VECTOR
+
+    def fld(lat, kind, nmu, prec, arr, layout=su3s.SOA, block=64):
+        f = su3s.Field(lat, kind, nmu, prec, layout, block)
+        f.upload(arr)
+        return f
+
+    if "volume" in which:
+        for L in (8, 16, 24, 32, 40, 48):
+            dims = (L, L, L, L)
+            v = synth.volume(dims)
+            lat = su3s.Lattice(dims)
+            a = fld(lat, MAT, 1, F64, synth.su3(SEED, 0, v))
+            b = fld(lat, MAT, 1, F64, synth.su3(SEED, 1, v))
+            x = fld(lat, VEC, 1, F64, synth.gauss_vector(SEED, 4, v))
+            la = fld(lat, MAT, 4, F64, synth.su3(SEED, 0, 4 * v))
+            lb = fld(lat, MAT, 4, F64, synth.su3(SEED, 1, 4 * v))
+            z, zv, zl = a.like(), x.like(), la.like()
+            res = {}
+            for name, dest, e, bps in (("A2", z, a * b, B_MM), ("A3", zv, a * x, B_MV),
+                                       ("A4", zl, la * lb, 4 * B_MM)):
+                ms = _time_ms(torch, stream, lambda: su3s.evaluate(dest, e, 0, stream))
+                res[name] = {"ms": round(ms, 5), "GB_s": round(bps * v / ms / 1e6, 1),
+                             "Gsites_s": round(v / ms / 1e6, 3)}
+            out.append({"study": "volume sweep", "L": L, "sites": v,
+                        "l2_resident": (3 * 144 * v) < 129e6, **res})
+            del a, b, x, la, lb, z, zv, zl
+            torch.cuda.empty_cache()
+
+    if "fused" in which:
+        dims = (32, 32, 32, 32)
+        v = synth.volume(dims)
+        lat = su3s.Lattice(dims)
+        F = {n: fld(lat, MAT, 1, F64, synth.su3(SEED + 1, i, v)) for i, n in enumerate("abcd")}
+        a, b, c, d = (F[n] for n in "abcd")
+        z, t1, t2 = a.like(), a.like(), a.like()
+        for name, fused, steps, fused_b, tbt_b in (
+                ("a*b+c*d", a * b + c * d,
+                 [(t1, a * b), (t2, c * d), (z, t1 + t2)], B_E1, 3 * 432),
+                ("a*b*c+0.5*d", a * b * c + 0.5 * d,
+                 [(t1, a * b), (t2, t1 * c), (z, t2 + 0.5 * d)], B_E2, 3 * 432),
+                ("adj(a)*b-b*adj(a)", a.adj() * b - b * a.adj(),
+                 [(t1, a.adj() * b), (t2, b * a.adj()), (z, t1 - t2)], B_E3, 3 * 432)):
+            ms_f = _time_ms(torch, stream, lambda: su3s.evaluate(z, fused, 0, stream))
+
+            def tbt():
+                for dst, e in steps:
+                    su3s.evaluate(dst, e, 0, stream)
+            ms_t = _time_ms(torch, stream, tbt)
+            out.append({"study": "fused vs term-by-term", "tree": name, "lattice": list(dims),
+                        "fused_ms": round(ms_f, 5), "term_by_term_ms": round(ms_t, 5),
+                        "speedup": round(ms_t / ms_f, 3), "fused_B_per_site": fused_b,
+                        "term_by_term_B_per_site": tbt_b})
+        del F, a, b, c, d, z, t1, t2
+        torch.cuda.empty_cache()
+
+    if "precision" in which:
+        fmts = [("f64", F64, None), ("f32", su3s.F32, "f32"), ("bf16", su3s.BF16, "bf16"),
+                ("f16", su3s.F16, "f16"), ("f64_c12", su3s.F64_C12, None),
+                ("f32_c12", su3s.F32_C12, "f32")]
+        for dims in ((32, 32, 32, 32), (16, 16, 16, 32)):
+            v = synth.volume(dims)
+            lat = su3s.Lattice(dims)
+            ha, hb = synth.su3(SEED + 2, 0, v), synth.su3(SEED + 2, 1, v)
+            exact = oracle.mm(ha, hb)
+            for name, prec, fmt in fmts:
+                a, b = fld(lat, MAT, 1, prec, ha), fld(lat, MAT, 1, prec, hb)
+                z = a.like()
+                ms = _time_ms(torch, stream, lambda: su3s.evaluate(z, a * b, 0, stream))
+                got = z.download()
+                bps = {"f64": B_MM, "f32": B_F32, "bf16": B_H, "f16": B_H, "f64_c12": B_C12,
+                       "f32_c12": B_C12F}[name]
+                out.append({"study": "precision", "lattice": list(dims), "storage": name,
+                            "max_abs_err_vs_fp64_oracle": float(np.abs(got - exact).max()),
+                            "ms": round(ms, 5), "Gsites_s": round(v / ms / 1e6, 3),
+                            "GB_s": round(bps * v / ms / 1e6, 1)})
+                del a, b, z
+            torch.cuda.empty_cache()
+
+    if "error" in which:
+        # FP64-storage results against the oracle: pair arithmetic vs native FP64
+        trees = [("a*b", ("mul", ("leaf", "a"), ("leaf", "b"))),
+                 ("a*b+c*d", ("add", ("mul", ("leaf", "a"), ("leaf", "b")),
+                              ("mul", ("leaf", "c"), ("leaf", "d")))),
+                 ("a*b*c+0.5*d", ("add", ("mul", ("mul", ("leaf", "a"), ("leaf", "b")),
+                                          ("leaf", "c")), ("scale", 0.5, ("leaf", "d")))),
+                 ("adj(a)*b-b*adj(a)", ("sub", ("mul", ("adj", ("leaf", "a")), ("leaf", "b")),
+                                        ("mul", ("leaf", "b"), ("adj", ("leaf", "a")))))]
+        for dims in ((32, 32, 32, 32), (48, 48, 48, 48)):
+            v = synth.volume(dims)
+            lat = su3s.Lattice(dims)
+            host = {n: synth.su3(SEED + 5, i, v) for i, n in enumerate("abcd")}
+            F = {n: fld(lat, MAT, 1, F64, host[n]) for n in "abcd"}
+            a, b, c, d = (F[n] for n in "abcd")
+            exprs = {"a*b": a * b, "a*b+c*d": a * b + c * d, "a*b*c+0.5*d": a * b * c + 0.5 * d,
+                     "adj(a)*b-b*adj(a)": a.adj() * b - b * a.adj()}
+            z = a.like()
+            for name, tree in trees:
+                if dims[0] == 48 and name != "a*b":
+                    continue
+                ref = oracle.eval_tree(tree, host)
+                errs = {}
+                for mname, m in (("df32", su3s.MATH_DF32), ("f64", su3s.MATH_F64)):
+                    su3s.evaluate(z, exprs[name], m, stream)
+                    stream.synchronize()
+                    errs[mname] = float(np.abs(z.download() - ref).max())
+                out.append({"study": "fp64 error vs oracle", "lattice": list(dims), "tree": name,
+                            "outputs": int(ref.size), "max_abs_err_df32": errs["df32"],
+                            "max_abs_err_native_f64": errs["f64"]})
+            del F, a, b, c, d, z, exprs
+            torch.cuda.empty_cache()
+
+    if "batch" in which:
+        picks = (synth.uniform_real(SEED + 3, 40, 64) + 1.0) / 2.0 * len(BATCH_SHAPES)
+        batch = su3s.Batch()
+        items, sites = [], 0
+        for i, p in enumerate(picks):
+            dims = BATCH_SHAPES[min(int(p), len(BATCH_SHAPES) - 1)]
+            lat = su3s.Lattice(dims)
+            nv = synth.volume(dims)
+            fs = {n: fld(lat, MAT, 1, F64, synth.su3(SEED + 3 + 1000 * i, j, nv))
+                  for j, n in enumerate("abcd")}
+            zb = fs["a"].like()
+            e = fs["a"] * fs["b"] + fs["c"] * fs["d"]
+            batch.add(zb, e)
+            items.append((lat, fs, zb, e))
+            sites += nv
+        batch.build()
+        ms_g = _time_ms(torch, stream, lambda: batch.launch(stream))
+
+        def separate():
+            for _, _, zb, e in items:
+                su3s.evaluate(zb, e, 0, stream)
+        ms_s = _time_ms(torch, stream, separate)
+        out.append({"study": "batched vs separate launches", "lattices": 64, "sites": sites,
+                    "graph_ms": round(ms_g, 5), "separate_ms": round(ms_s, 5),
+                    "speedup": round(ms_s / ms_g, 3),
+                    "graph_GB_s": round(B_E1 * sites / ms_g / 1e6, 1),
+                    "separate_GB_s": round(B_E1 * sites / ms_s / 1e6, 1)})
+        del batch, items
+        torch.cuda.empty_cache()
+
+    if "layout" in which:
+        dims = DIMS
+        v = synth.volume(dims)
+        lat = su3s.Lattice(dims)
+        ha, hb = synth.su3(SEED, 0, v), synth.su3(SEED, 1, v)
+        for layout, block in ((su3s.SOA, 0), (su3s.AOSOA, 4), (su3s.AOSOA, 16), (su3s.AOSOA, 32),
+                              (su3s.AOSOA, 64), (su3s.AOSOA, 128), (su3s.AOSOA, 256),
+                              (su3s.AOSOA, 1024)):
+            a = fld(lat, MAT, 1, F64, ha, layout, block or 64)
+            b = fld(lat, MAT, 1, F64, hb, layout, block or 64)
+            z = a.like()
+            for pipe, pname in ((su3s.PIPE_PLAIN, "plain"), (su3s.PIPE_TMA, "tma")):
+                su3s.set_pipeline(pipe)
+                ms = _time_ms(torch, stream, lambda: su3s.evaluate(z, a * b, 0, stream))
+                out.append({"study": "layout sweep z=a*b", "lattice": list(dims),
+                            "layout": "soa" if layout == su3s.SOA else "aosoa%d" % block,
+                            "pipeline": pname, "ms": round(ms, 5),
+                            "GB_s": round(B_MM * v / ms / 1e6, 1)})
+            su3s.set_pipeline(su3s.PIPE_AUTO)
+            del a, b, z
+            torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -413,6 +638,9 @@ def main():
     ap.add_argument("--rows", default="",
                     help="comma-separated row-name prefixes to run (default: every row)")
     ap.add_argument("--dims", default="48,48,48,48", help="lattice extents (default 48^4)")
+    ap.add_argument("--study", default="",
+                    help="comma list of studies to run instead of the step: volume, fused, "
+                         "precision, error, batch, layout (one JSON line each)")
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "tma", "tma_leaf"],
                     help="data movement of FP64-storage kernels (default: the library's choice)")
     args = ap.parse_args()
@@ -455,6 +683,11 @@ def main():
     import paper_1710_09409_gb300 as su3s
     import synth
     su3s.load()
+    if args.study:
+        st = torch.cuda.Stream()
+        for line in run_studies(su3s, synth, torch, st, args.study.split(",")):
+            print(json.dumps(line))
+        return 0
     su3s.set_pipeline({"auto": su3s.PIPE_AUTO, "plain": su3s.PIPE_PLAIN, "tma": su3s.PIPE_TMA,
                        "tma_leaf": su3s.PIPE_TMA_LEAF}[args.pipeline])
     stream = torch.cuda.Stream()

@@ -254,8 +254,9 @@ int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int th
  *       with bulk copies into shared memory while it computes the current one;
  *    2  TMA-staged per leaf: each leaf has its own buffer and barrier, is read
  *       when first needed and refilled after its last use.
- * Staging needs 32 sites of a component to be contiguous (SOA, or AOSOA with
- * block >= 32); otherwise plain loads are used.  EINVAL for other values. */
+ * All modes give bitwise identical results.  Staging needs 32 sites of a
+ * component to be contiguous (SOA, or AOSOA with block >= 32); otherwise plain
+ * loads are used.  EINVAL for other values. */
 int su3s_set_pipeline(int mode);
 
 /* Read and clear the library's device error word (a stream-ordered copy

@@ -133,7 +133,8 @@ static std::map<std::tuple<const void*, int64_t, int>, Geo> g_geo;
 
 void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int bps, int variant) {
   std::lock_guard<std::mutex> lk(g_geo_mu);
-  g_geo[std::make_tuple(kernel, nvec, nmu)] = Geo{threads, bps, variant};
+  Geo g{threads, bps, variant};
+  g_geo[std::make_tuple(kernel, nvec, nmu)] = g;
 }
 
 static bool find_geometry(const void* kernel, int64_t nvec, int nmu, Geo* g) {
@@ -170,7 +171,7 @@ int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* 
   find_geometry(e->kernel[0], nvec, nmu, &g);
   const bool can_stage = e->fn[1] && tma_ok && nvec % 32 == 0;
   int variant = g.variant;
-  if (variant < 0 || variant >= kNumVariants) variant = e->default_variant;
+  if (variant < 0 || variant >= kNumVariants || !e->fn[variant]) variant = e->default_variant;
   if (!can_stage) variant = 0;
   if (variant > 0) {
     int threads = g.threads > 0 ? g.threads : 128;
@@ -744,9 +745,15 @@ SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* 
   const bool tma = ent->fn[1] && tma_layout_ok(dest) && p.nvec % 32 == 0;
   float best = 1e30f;
   int bt = 256, bb = 0, bv = 0;
+  struct Cand {
+    int var, th, bps;
+  };
+  std::vector<Cand> cands;
   for (int var = 0; var < (tma ? kNumVariants : 1); ++var)
     for (int th : th_c)
-      for (int bps : bps_c) {
+      for (int bps : bps_c) cands.push_back(Cand{var, th, bps});
+  for (const Cand& cd : cands) {
+        const int var = cd.var, th = cd.th, bps = cd.bps;
         set_geometry(ent->kernel[0], p.nvec, p.nmu, th, bps, var);
         Launch L;
         plan_launch(ent, p.nvec, p.nmu, tma, &L);
@@ -772,9 +779,9 @@ SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* 
           best = ms;
           bt = th;
           bb = bps;
-          bv = var;
+          bv = L.variant;
         }
-      }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   set_geometry(ent->kernel[0], p.nvec, p.nmu, bt, bb, bv);

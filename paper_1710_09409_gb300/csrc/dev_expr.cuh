@@ -271,6 +271,62 @@ __device__ __forceinline__ void outer_acc(typename M::A* z, const typename M::R*
     }
 }
 
+// z += SG * op(x) * op(y), each output accumulated on its own and then added
+// to z exactly (the sum of two products keeps two independent accumulations
+// per output, which halves the rounding error of the pair arithmetic's tail).
+template <class M, int SG, bool AX, bool AY>
+__device__ __forceinline__ void mm_combine(typename M::A* z, const typename M::R* x,
+                                           const typename M::R* y) {
+  constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      typename M::A re, im;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int xi = AX ? (3 * j + i) : (3 * i + j);
+        const int yi = AY ? (3 * k + j) : (3 * j + k);
+        if (j == 0) {
+          M::template fma<true, 1>(re, x[2 * xi], y[2 * yi]);
+          M::template fma<true, sy>(im, x[2 * xi], y[2 * yi + 1]);
+        } else {
+          M::template fma<false, 1>(re, x[2 * xi], y[2 * yi]);
+          M::template fma<false, sy>(im, x[2 * xi], y[2 * yi + 1]);
+        }
+        M::template fma<false, -sx * sy>(re, x[2 * xi + 1], y[2 * yi + 1]);
+        M::template fma<false, sx>(im, x[2 * xi + 1], y[2 * yi]);
+      }
+      M::template combine<SG>(z[2 * (3 * i + k)], re);
+      M::template combine<SG>(z[2 * (3 * i + k) + 1], im);
+    }
+}
+
+template <class M, int SG, bool AX>
+__device__ __forceinline__ void mv_combine(typename M::A* z, const typename M::R* x,
+                                           const typename M::R* v) {
+  constexpr int sx = AX ? -1 : 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    typename M::A re, im;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int xi = AX ? (3 * j + i) : (3 * i + j);
+      if (j == 0) {
+        M::template fma<true, 1>(re, x[2 * xi], v[2 * j]);
+        M::template fma<true, 1>(im, x[2 * xi], v[2 * j + 1]);
+      } else {
+        M::template fma<false, 1>(re, x[2 * xi], v[2 * j]);
+        M::template fma<false, 1>(im, x[2 * xi], v[2 * j + 1]);
+      }
+      M::template fma<false, -sx>(re, x[2 * xi + 1], v[2 * j + 1]);
+      M::template fma<false, sx>(im, x[2 * xi + 1], v[2 * j]);
+    }
+    M::template combine<SG>(z[2 * i], re);
+    M::template combine<SG>(z[2 * i + 1], im);
+  }
+}
+
 template <class M, int W, bool FIRST, int SG>
 __device__ __forceinline__ void vec_add(typename M::A* z, const typename M::R* x) {
 #pragma unroll
@@ -368,16 +424,49 @@ __device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Mul<X
   }
 }
 
+template <class T>
+struct IsMulNode {
+  static constexpr bool value = false;
+};
+template <class X, class Y>
+struct IsMulNode<Mul<X, Y>> {
+  static constexpr bool value = true;
+};
+
+// acc += SG * (product node), accumulated per output on its own and combined.
+template <class M, int SG, class C, class X, class Y>
+__device__ __forceinline__ void mul_combine(const C& ctx, typename M::A* acc, Mul<X, Y>*) {
+  using OX = Operand<X>;
+  using OY = Operand<Y>;
+  using BX = typename OX::base;
+  using BY = typename OY::base;
+  typename M::R xv[Width<BX::kind>::value];
+  typename M::R yv[Width<BY::kind>::value];
+  value<BX, M>(ctx, xv);
+  value<BY, M>(ctx, yv);
+  if constexpr (Mul<X, Y>::kind == KM) {
+    mm_combine<M, SG, OX::adj, OY::adj>(acc, xv, yv);
+  } else if constexpr (Mul<X, Y>::kind == KV) {
+    mv_combine<M, SG, OX::adj>(acc, xv, yv);
+  } else {
+    typename M::A t;
+    M::template fma<true, 1>(t, xv[0], yv[0]);
+    M::template combine<SG>(acc[0], t);
+  }
+}
+
 template <class M, bool FIRST, int SG, class C, class X, class Y>
 __device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Add<X, Y>*) {
   acc_into<X, M, FIRST, SG>(ctx, acc);
-  acc_into<Y, M, false, SG>(ctx, acc);
+  if constexpr (IsMulNode<Y>::value && (IsMulNode<X>::value || FIRST)) mul_combine<M, SG>(ctx, acc, (Y*)nullptr);
+  else acc_into<Y, M, false, SG>(ctx, acc);
 }
 
 template <class M, bool FIRST, int SG, class C, class X, class Y>
 __device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Sub<X, Y>*) {
   acc_into<X, M, FIRST, SG>(ctx, acc);
-  acc_into<Y, M, false, -SG>(ctx, acc);
+  if constexpr (IsMulNode<Y>::value && (IsMulNode<X>::value || FIRST)) mul_combine<M, -SG>(ctx, acc, (Y*)nullptr);
+  else acc_into<Y, M, false, -SG>(ctx, acc);
 }
 
 template <class M, bool FIRST, int SG, class C, int K, class X>
@@ -443,6 +532,9 @@ struct Rev {
     }
   }
 
+  // Z = op(BX) op(BY).  The gradient of each operand needs G and the other
+  // operand only, so the other operand is fetched just before its use: Y's
+  // value, then d(BX); X's value, then d(BY).  One operand is live at a time.
   template <class M, class C, class GA, class Sink, class X, class Y>
   __device__ static __forceinline__ void node(const C& ctx, const typename M::R* G, GA& ga,
                                               Sink& sink, Mul<X, Y>*) {
@@ -451,34 +543,42 @@ struct Rev {
     using BX = typename OX::base;
     using BY = typename OY::base;
     constexpr bool ax = OX::adj, ay = OY::adj;
-    typename M::R xv[Width<BX::kind>::value];
-    typename M::R yv[Width<BY::kind>::value];
-    value<BX, M>(ctx, xv);
-    value<BY, M>(ctx, yv);
-    if constexpr (Mul<X, Y>::kind == KM) {
-      // d(base X): ax ? (Y G^dagger) : (G Y^dagger), with Y = op(BY)
-      feed<BX, M>(ctx, ga, sink, [&](typename M::A* a) {
-        if constexpr (ax) mm_acc<M, true, 1, ay, true>(a, yv, G);
-        else mm_acc<M, true, 1, false, !ay>(a, G, yv);
-      });
-      // d(base Y): ay ? (G^dagger X) : (X^dagger G), with X = op(BX)
-      feed<BY, M>(ctx, ga, sink, [&](typename M::A* a) {
-        if constexpr (ay) mm_acc<M, true, 1, true, ax>(a, G, xv);
-        else mm_acc<M, true, 1, !ax, false>(a, xv, G);
-      });
-    } else if constexpr (Mul<X, Y>::kind == KV) {
-      // Z = op(BX) v: d op(BX) = G v^dagger; d(BX) = ax ? v G^dagger : G v^dagger
-      feed<BX, M>(ctx, ga, sink, [&](typename M::A* a) {
-        if constexpr (ax) outer_acc<M, true, 1>(a, yv, G);
-        else outer_acc<M, true, 1>(a, G, yv);
-      });
-      // dv = op(BX)^dagger G
-      feed<BY, M>(ctx, ga, sink, [&](typename M::A* a) { mv_acc<M, true, 1, !ax>(a, xv, G); });
-    } else {
-      feed<BX, M>(ctx, ga, sink,
-                  [&](typename M::A* a) { M::template fma<true, 1>(a[0], G[0], yv[0]); });
-      feed<BY, M>(ctx, ga, sink,
-                  [&](typename M::A* a) { M::template fma<true, 1>(a[0], xv[0], G[0]); });
+    {
+      typename M::R yv[Width<BY::kind>::value];
+      value<BY, M>(ctx, yv);
+      if constexpr (Mul<X, Y>::kind == KM) {
+        // d(base X): ax ? (Y G^dagger) : (G Y^dagger), with Y = op(BY)
+        feed<BX, M>(ctx, ga, sink, [&](typename M::A* a) {
+          if constexpr (ax) mm_acc<M, true, 1, ay, true>(a, yv, G);
+          else mm_acc<M, true, 1, false, !ay>(a, G, yv);
+        });
+      } else if constexpr (Mul<X, Y>::kind == KV) {
+        // Z = op(BX) v: d op(BX) = G v^dagger; d(BX) = ax ? v G^dagger : G v^dagger
+        feed<BX, M>(ctx, ga, sink, [&](typename M::A* a) {
+          if constexpr (ax) outer_acc<M, true, 1>(a, yv, G);
+          else outer_acc<M, true, 1>(a, G, yv);
+        });
+      } else {
+        feed<BX, M>(ctx, ga, sink,
+                    [&](typename M::A* a) { M::template fma<true, 1>(a[0], G[0], yv[0]); });
+      }
+    }
+    {
+      typename M::R xv[Width<BX::kind>::value];
+      value<BX, M>(ctx, xv);
+      if constexpr (Mul<X, Y>::kind == KM) {
+        // d(base Y): ay ? (G^dagger X) : (X^dagger G), with X = op(BX)
+        feed<BY, M>(ctx, ga, sink, [&](typename M::A* a) {
+          if constexpr (ay) mm_acc<M, true, 1, true, ax>(a, G, xv);
+          else mm_acc<M, true, 1, !ax, false>(a, xv, G);
+        });
+      } else if constexpr (Mul<X, Y>::kind == KV) {
+        // dv = op(BX)^dagger G
+        feed<BY, M>(ctx, ga, sink, [&](typename M::A* a) { mv_acc<M, true, 1, !ax>(a, xv, G); });
+      } else {
+        feed<BY, M>(ctx, ga, sink,
+                    [&](typename M::A* a) { M::template fma<true, 1>(a[0], xv[0], G[0]); });
+      }
     }
   }
 

@@ -151,12 +151,30 @@ __device__ __forceinline__ void eval_sites(const KParams& p, int64_t t, int mu) 
   store_obj<Tree::kind, PREC, M, VPS, W>(p.dst, s, mu, acc);
 }
 
+// Units of work a thread (plain loads: site vectors) or a warp (staged: 32-site
+// tiles) takes: first, first + stride, ... below end.
+struct Range {
+  int64_t first, end, stride;
+};
+
+__device__ __forceinline__ Range thread_range(int64_t end) {
+  return Range{(int64_t)blockIdx.x * blockDim.x + threadIdx.x, end,
+               (int64_t)gridDim.x * blockDim.x};
+}
+__device__ __forceinline__ Range warp_range(int64_t end) {
+  const int nw = blockDim.x >> 5;
+  return Range{(int64_t)blockIdx.x * nw + (threadIdx.x >> 5), end, (int64_t)gridDim.x * nw};
+}
+
+template <class Tree, class M, int PREC>
+__device__ __forceinline__ void plain_range(const KParams& p, Range r) {
+  const int mu = blockIdx.y;
+  for (int64_t t = r.first; t < r.end; t += r.stride) eval_sites<Tree, M, PREC>(p, t, mu);
+}
+
 template <class Tree, class M, int PREC>
 __global__ void __launch_bounds__(256) k_eval(const __grid_constant__ KParams p) {
-  const int mu = blockIdx.y;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < p.nvec; t += stride)
-    eval_sites<Tree, M, PREC>(p, t, mu);
+  plain_range<Tree, M, PREC>(p, thread_range(p.nvec));
 }
 
 // ------------------------------------------------------------ reverse kernel
@@ -186,13 +204,12 @@ __device__ __forceinline__ void store_repeated(GA& ga, Sink& sink) {
 }
 
 template <class Tree, class M>
-__global__ void __launch_bounds__(256) k_adjoint(const __grid_constant__ GParams p) {
+__device__ __forceinline__ void adj_plain_range(const GParams& p, Range rg) {
   constexpr int NL = Tree::nleaf;
   constexpr int NS = Tree::nsc;
   constexpr int W = Width<Tree::kind>::value;
   const int mu = blockIdx.y;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.k.nvec; s += stride) {
+  for (int64_t s = rg.first; s < rg.end; s += rg.stride) {
     Ctx<M, NL, NS> ctx[1];
 #pragma unroll
     for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
@@ -211,6 +228,11 @@ __global__ void __launch_bounds__(256) k_adjoint(const __grid_constant__ GParams
     store_repeated<Tree, 0, M>(ga, sink);
     (void)W;
   }
+}
+
+template <class Tree, class M>
+__global__ void __launch_bounds__(256) k_adjoint(const __grid_constant__ GParams p) {
+  adj_plain_range<Tree, M>(p, thread_range(p.k.nvec));
 }
 
 // ------------------------------------------------- TMA-staged variants
@@ -335,20 +357,18 @@ __device__ __forceinline__ void read_leaves(const unsigned char* buf, int lane, 
 }
 
 template <class Tree, class M, int PREC>
-__global__ void __launch_bounds__(256) k_eval_tma(const __grid_constant__ KParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned char* smem) {
   constexpr int NL = Tree::nleaf;
   constexpr int NS = Tree::nsc;
   constexpr int W = Width<Tree::kind>::value;
   constexpr int TB = TileBytes<Tree, PREC, false>::value;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   unsigned char* buf = smem + warp * (TB + 16);
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf + TB);
   const int mu = blockIdx.y;
-  const int64_t ntiles = p.nvec >> 5;
-  const int64_t wstride = (int64_t)gridDim.x * nwarps;
-  int64_t t = (int64_t)blockIdx.x * nwarps + warp;
+  const int64_t ntiles = rg.end;
+  const int64_t wstride = rg.stride;
+  int64_t t = rg.first;
   if (lane == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
@@ -385,21 +405,25 @@ __global__ void __launch_bounds__(256) k_eval_tma(const __grid_constant__ KParam
   }
 }
 
-template <class Tree, class M>
-__global__ void __launch_bounds__(256) k_adjoint_tma(const __grid_constant__ GParams p) {
+template <class Tree, class M, int PREC>
+__global__ void __launch_bounds__(256) k_eval_tma(const __grid_constant__ KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
+  tma_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);
+}
+
+template <class Tree, class M>
+__device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsigned char* smem) {
   constexpr int NL = Tree::nleaf;
   constexpr int NS = Tree::nsc;
   constexpr int TB = TileBytes<Tree, P_F64, true>::value;
   constexpr int GOFF = LeafOff<Tree, P_F64, NL>::value;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   unsigned char* buf = smem + warp * (TB + 16);
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf + TB);
   const int mu = blockIdx.y;
-  const int64_t ntiles = p.k.nvec >> 5;
-  const int64_t wstride = (int64_t)gridDim.x * nwarps;
-  int64_t t = (int64_t)blockIdx.x * nwarps + warp;
+  const int64_t ntiles = rg.end;
+  const int64_t wstride = rg.stride;
+  int64_t t = rg.first;
   if (lane == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
@@ -435,6 +459,12 @@ __global__ void __launch_bounds__(256) k_adjoint_tma(const __grid_constant__ GPa
     store_repeated<Tree, 0, M>(ga, sink);
     t = tn;
   }
+}
+
+template <class Tree, class M>
+__global__ void __launch_bounds__(256) k_adjoint_tma(const __grid_constant__ GParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  adj_tma_range<Tree, M>(p, warp_range(p.k.nvec >> 5), smem);
 }
 
 // ------------------------------------------- lazily staged (per-leaf) variant
@@ -597,15 +627,13 @@ __device__ __forceinline__ void lazy_setup(LazyCtx<Tree, M, PREC, GRAD>& c, unsi
 }
 
 template <class Tree, class M, int PREC>
-__global__ void __launch_bounds__(128, 4) k_eval_lazy(const __grid_constant__ KParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void lazy_range(const KParams& p, Range rg, unsigned char* smem) {
   constexpr int W = Width<Tree::kind>::value;
   LazyCtx<Tree, M, PREC, false> c;
   lazy_setup(c, smem, p, nullptr);
-  const int nwarps = blockDim.x >> 5;
-  const int64_t ntiles = p.nvec >> 5;
-  const int64_t wstride = (int64_t)gridDim.x * nwarps;
-  int64_t t = (int64_t)blockIdx.x * nwarps + (threadIdx.x >> 5);
+  const int64_t ntiles = rg.end;
+  const int64_t wstride = rg.stride;
+  int64_t t = rg.first;
   if (t < ntiles) c.template issue_all<0>(t << 5);
   while (t < ntiles) {
     const int64_t tn = t + wstride;
@@ -629,17 +657,21 @@ __global__ void __launch_bounds__(128, 4) k_eval_lazy(const __grid_constant__ KP
   if (c.dead) c.template drain<0>();
 }
 
-template <class Tree, class M>
-__global__ void __launch_bounds__(128, 4) k_adjoint_lazy(const __grid_constant__ GParams p) {
+template <class Tree, class M, int PREC>
+__global__ void __launch_bounds__(128, 4) k_eval_lazy(const __grid_constant__ KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
+  lazy_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);
+}
+
+template <class Tree, class M>
+__device__ __forceinline__ void adj_lazy_range(const GParams& p, Range rg, unsigned char* smem) {
   constexpr int NL = Tree::nleaf;
   constexpr int W = Width<Tree::kind>::value;
   LazyCtx<Tree, M, P_F64, true> c;
   lazy_setup(c, smem, p.k, &p.gout);
-  const int nwarps = blockDim.x >> 5;
-  const int64_t ntiles = p.k.nvec >> 5;
-  const int64_t wstride = (int64_t)gridDim.x * nwarps;
-  int64_t t = (int64_t)blockIdx.x * nwarps + (threadIdx.x >> 5);
+  const int64_t ntiles = rg.end;
+  const int64_t wstride = rg.stride;
+  int64_t t = rg.first;
   if (t < ntiles) c.template issue_all<0>(t << 5);
   while (t < ntiles) {
     const int64_t tn = t + wstride;
@@ -661,6 +693,12 @@ __global__ void __launch_bounds__(128, 4) k_adjoint_lazy(const __grid_constant__
     t = tn;
   }
   if (c.dead) c.template drain<0>();
+}
+
+template <class Tree, class M>
+__global__ void __launch_bounds__(128, 3) k_adjoint_lazy(const __grid_constant__ GParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  adj_lazy_range<Tree, M>(p, warp_range(p.k.nvec >> 5), smem);
 }
 
 // ------------------------------------------------------------ launchers
@@ -784,8 +822,8 @@ struct Sig<Adj<X>> {
 // Default data movement of a tree (measured on the GB300 at 48^4, FP64
 // storage, pair arithmetic): trees that read a leaf twice or nest products are
 // issue-bound and keep plain loads; trees of at most two leaves stage whole
-// tiles; sums of products of distinct leaves stage leaf by leaf.  Reverse
-// mode stages whole tiles for products and sums of products.
+// tiles; sums of products of distinct leaves stage leaf by leaf, in forward
+// and reverse mode.
 template <class T, int I>
 struct AnyRepeat {
   static constexpr bool value = Count<T, I>::value > 1 || AnyRepeat<T, I - 1>::value;
@@ -822,12 +860,12 @@ template <class Tree, bool GRAD>
 constexpr int default_variant() {
   if (AnyRepeat<Tree, Tree::nleaf - 1>::value) return 0;
   if (Tree::nleaf <= 2) return 1;
-  if (IsSumOfProds<Tree>::value) return GRAD ? 1 : 2;
+  if (IsSumOfProds<Tree>::value) return 2;
   return 0;
 }
 
-// Kernel variants of one tree: plain loads, TMA-staged eagerly (whole tile),
-// TMA-staged lazily (per leaf).  The staged variants exist for FP64 storage.
+// Kernel variants of one tree: 0 plain loads, 1 TMA-staged eagerly (whole
+// tile), 2 TMA-staged lazily (per leaf).  1 and 2 exist for FP64 storage.
 struct Variants {
   LaunchFn fn[3];
   const void* kernel[3];

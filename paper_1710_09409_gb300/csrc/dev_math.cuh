@@ -14,10 +14,10 @@
 //                the leading products xh*yh and an FP32 tail `lo`; each new
 //                leading product enters S through Knuth's TwoSum, whose error
 //                term is taken with an FMA against the exact product so the
-//                product's own rounding error folds in; the cross terms
-//                xh*yl + xl*yh go into the tail by FMA (Dekker/Knuth
-//                error-free transformations, Ogita-Rump-Oishi style dot
-//                product);
+//                product's own rounding error folds in; that error and the
+//                cross terms xh*yl + xl*yh are gathered per term and enter the
+//                tail with one rounding (Dekker/Knuth error-free
+//                transformations, Ogita-Rump-Oishi style dot product);
 //              * the result S + lo is rounded toward zero into one FP32 value
 //                plus a same-signed remainder, and the FP64 bit pattern is
 //                assembled with integer operations: the leading value gives
@@ -101,6 +101,11 @@ struct MathF64 {
     if (FIRST) a = (SG > 0) ? x : -x;
     else a = (SG > 0) ? __dadd_rn(a, x) : __dsub_rn(a, x);
   }
+  // a += sg * b for two accumulators
+  template <int SG>
+  __device__ static __forceinline__ void combine(A& a, const A& b) {
+    a = (SG > 0) ? __dadd_rn(a, b) : __dsub_rn(a, b);
+  }
 };
 
 // -------------------------------------------------------------- MathDF
@@ -137,13 +142,30 @@ struct MathDF {
       const float ap = __fsub_rn(s, bp);
       const float db = __fmaf_rn(xh, y.h, -bp);  // exact product minus bp, one rounding
       const float da = __fsub_rn(a.S, ap);
-      float lo = __fadd_rn(a.lo, da);
-      lo = __fadd_rn(lo, db);
-      lo = __fmaf_rn(xh, y.l, lo);
-      lo = __fmaf_rn(xl, y.h, lo);
+      // this term's small parts (sum error, cross terms) are gathered first and
+      // enter the running tail with a single rounding
+      float t = __fadd_rn(da, db);
+      t = __fmaf_rn(xl, y.h, t);
+      t = __fmaf_rn(xh, y.l, t);
       a.S = s;
-      a.lo = lo;
+      a.lo = __fadd_rn(a.lo, t);
     }
+  }
+
+  // a += sg * b for two accumulators: TwoSum of the leading parts, tails added
+  template <int SG>
+  __device__ static __forceinline__ void combine(A& a, const A& b0) {
+    const float bS = SG > 0 ? b0.S : -b0.S;
+    const float bl = SG > 0 ? b0.lo : -b0.lo;
+    const float s = __fadd_rn(a.S, bS);
+    const float bp = __fsub_rn(s, a.S);
+    const float ap = __fsub_rn(s, bp);
+    const float db = __fsub_rn(bS, bp);
+    const float da = __fsub_rn(a.S, ap);
+    float t = __fadd_rn(da, db);
+    t = __fadd_rn(t, bl);
+    a.S = s;
+    a.lo = __fadd_rn(a.lo, t);
   }
 
   template <bool FIRST, int SG>
@@ -159,11 +181,10 @@ struct MathDF {
       const float ap = __fsub_rn(s, bp);
       const float db = __fsub_rn(xh, bp);
       const float da = __fsub_rn(a.S, ap);
-      float lo = __fadd_rn(a.lo, da);
-      lo = __fadd_rn(lo, db);
-      lo = __fadd_rn(lo, xl);
+      float t = __fadd_rn(da, db);
+      t = __fadd_rn(t, xl);
       a.S = s;
-      a.lo = lo;
+      a.lo = __fadd_rn(a.lo, t);
     }
   }
 };
@@ -187,6 +208,10 @@ struct MathF32 {
   __device__ static __forceinline__ void add(A& a, const R& x) {
     if (FIRST) a = (SG > 0) ? x : -x;
     else a = (SG > 0) ? __fadd_rn(a, x) : __fsub_rn(a, x);
+  }
+  template <int SG>
+  __device__ static __forceinline__ void combine(A& a, const A& b) {
+    a = (SG > 0) ? __fadd_rn(a, b) : __fsub_rn(a, b);
   }
 };
 
