@@ -47,6 +47,31 @@ ROW_NAMES = ["A2 z=a*b", "A3 z=a*v", "A4 z_mu=a_mu*b_mu", "A5 z=a*b+c*d", "A5 z=
              "A9 adjoint of z=a*b", "A9 adjoint of z=a*b+c*d"]
 ROW_A8, ROW_A9A, ROW_A9B = ROW_NAMES[11], ROW_NAMES[12], ROW_NAMES[13]
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on a
+# 32^4 lattice (1,048,576 sites), from one ncu capture of the kernels as they
+# stand; scaled to the benchmark's volume in proportion to the sites (the
+# algorithmic bytes).  (row, kernel whose counters these are, bytes, algorithmic
+# bytes of that launch).  A row missing here reports traffic null.
+TRAFFIC_32 = {
+    "A2 z=a*b": ("k_eval_tma<Mul<LM<0>,LM<1>>,MathDF,0>", (302.0 + 112.3) * 1e6, 432 * 1048576),
+    "A4 z_mu=a_mu*b_mu": ("k_eval_tma<Mul<LM<0>,LM<1>>,MathDF,0>", (1208.0 + 570.5) * 1e6,
+                          4 * 432 * 1048576),
+    "A5 z=a*b+c*d": ("k_eval_lazy<E1,MathDF,0>", (604.8 + 125.4) * 1e6, 720 * 1048576),
+    "A5 z=a*b*c+0.5*d": ("k_eval<E2,MathDF,0>", (604.1 + 123.3) * 1e6, 720 * 1048576),
+    "A5 z=adj(a)*b-b*adj(a)": ("k_eval<E3,MathDF,0>", (302.1 + 110.4) * 1e6, 432 * 1048576),
+    "A9 adjoint of z=a*b": ("k_adjoint_tma<MM,MathDF>", (453.1 + 253.5) * 1e6, 720 * 1048576),
+    "A9 adjoint of z=a*b+c*d": ("k_adjoint_lazy<E1,MathDF>", (755.3 + 550.5) * 1e6,
+                                1296 * 1048576),
+}
+
+
+def traffic_bytes(row_name, nbytes):
+    """Measured DRAM bytes of one launch of a row's kernel, scaled to nbytes."""
+    t = TRAFFIC_32.get(row_name)
+    if t is None:
+        return None
+    return int(round(t[1] * nbytes / t[2]))
+
 
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -726,7 +751,8 @@ def main():
     roof = {"bound": "hbm", "kernel": rows[di].name, "achieved": round(achieved, 1),
             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-            else "fallback 6800 GB/s", "traffic": None,
+            else "fallback 6800 GB/s", "traffic": traffic_bytes(rows[di].name, rows[di].nbytes),
+            "traffic_source": "ncu dram__bytes_read+write at 32^4, scaled by sites",
             "algorithmic_bytes_per_launch": rows[di].nbytes}
     a2 = row_out[0]
 
