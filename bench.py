@@ -46,6 +46,10 @@ ROW_NAMES = ["A2 z=a*b", "A3 z=a*v", "A4 z_mu=a_mu*b_mu", "A5 z=a*b+c*d", "A5 z=
              "A7 z=a*b f64_c12", "A7 z=a*b f32_c12", "A8 batch 64 lattices z=a*b+c*d",
              "A9 adjoint of z=a*b", "A9 adjoint of z=a*b+c*d"]
 ROW_A8, ROW_A9A, ROW_A9B = ROW_NAMES[11], ROW_NAMES[12], ROW_NAMES[13]
+MATH_NAMES = ("fx", "df32", "f64")
+MATH_IDS = {"f64": 1, "df32": 2, "fx": 3}
+MATH_DESC = {"fx": "shared-exponent fixed-point (fx)", "df32": "pair-of-FP32 (df32)",
+             "f64": "native FP64 (f64)"}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on a
 # 32^4 lattice (1,048,576 sites), from one ncu capture of the kernels as they
@@ -584,12 +588,13 @@ def run_studies(su3s, synth, torch, stream, which):
                     continue
                 ref = oracle.eval_tree(tree, host)
                 errs = {}
-                for mname, m in (("df32", su3s.MATH_DF32), ("f64", su3s.MATH_F64)):
-                    su3s.evaluate(z, exprs[name], m, stream)
+                for mname in MATH_NAMES:
+                    su3s.evaluate(z, exprs[name], MATH_IDS[mname], stream)
                     stream.synchronize()
                     errs[mname] = float(np.abs(z.download() - ref).max())
                 out.append({"study": "fp64 error vs oracle", "lattice": list(dims), "tree": name,
-                            "outputs": int(ref.size), "max_abs_err_df32": errs["df32"],
+                            "outputs": int(ref.size), "max_abs_err_fx": errs["fx"],
+                            "max_abs_err_df32": errs["df32"],
                             "max_abs_err_native_f64": errs["f64"]})
             del F, a, b, c, d, z, exprs
             torch.cuda.empty_cache()
@@ -666,6 +671,9 @@ def main():
     ap.add_argument("--study", default="",
                     help="comma list of studies to run instead of the step: volume, fused, "
                          "precision, error, batch, layout (one JSON line each)")
+    ap.add_argument("--math", default="df32", choices=["fx", "df32", "f64"],
+                    help="arithmetic of the FP64-storage rows in the step (the others are "
+                         "timed beside it)")
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "tma", "tma_leaf"],
                     help="data movement of FP64-storage kernels (default: the library's choice)")
     args = ap.parse_args()
@@ -708,6 +716,7 @@ def main():
     import paper_1710_09409_gb300 as su3s
     import synth
     su3s.load()
+    su3s.set_default_math(MATH_IDS[args.math])
     if args.study:
         st = torch.cuda.Stream()
         for line in run_studies(su3s, synth, torch, st, args.study.split(",")):
@@ -756,16 +765,17 @@ def main():
             "algorithmic_bytes_per_launch": rows[di].nbytes}
     a2 = row_out[0]
 
-    # native FP64 arithmetic for the FP64 rows, reported beside (not in the step)
+    # the other arithmetics for the FP64 rows, reported beside (not in the step)
     variants = []
-    su3s.set_default_math(su3s.MATH_F64)
-    for r in (rows if not args.no_variants else []):
-        if r.dtype == "f64" and not r.name.startswith("A8"):
-            _, pr, _ = time_step([r], torch, stream, 20, 2)
-            m = float(np.mean(pr[0]))
-            variants.append({"row": r.name, "math": "native f64", "ms": round(m, 5),
-                             "GB_s": round(r.nbytes / (m * 1e-3) / 1e9, 1)})
-    su3s.set_default_math(su3s.MATH_DF32)
+    for mname in [m for m in MATH_NAMES if m != args.math]:
+        su3s.set_default_math(MATH_IDS[mname])
+        for r in (rows if not args.no_variants else []):
+            if r.dtype == "f64":
+                _, pr, _ = time_step([r], torch, stream, 20, 2)
+                m = float(np.mean(pr[0]))
+                variants.append({"row": r.name, "math": mname, "ms": round(m, 5),
+                                 "GB_s": round(r.nbytes / (m * 1e-3) / 1e9, 1)})
+    su3s.set_default_math(MATH_IDS[args.math])
 
     e2e = None
     if with_host:
@@ -786,14 +796,14 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": ("48^4 lattice (5,308,416 sites), every hot-path row A2-A9 once "
-                                    "per step; FP64 rows in the library default arithmetic (df32)"
+                                    "per step; FP64 rows in %s arithmetic" % MATH_DESC[args.math]
                                     if full else "subset %s on %s" % (args.rows or "all rows",
                                                                       "x".join(map(str, dims)))),
                        "lattice": list(dims), "layout": "soa", "pipeline": args.pipeline,
                        "l2": "every field larger than the 129 MB L2; no flush needed",
                        "bytes_per_step": bytes_step, "seed": SEED},
             "sites_per_s": round(a2["Gsites_s"] * 1e9 * ws, 0),
-            "rows": row_out, "f64_native_rows": variants,
+            "rows": row_out, "other_arithmetic_rows": variants,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
         }

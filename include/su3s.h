@@ -65,6 +65,7 @@ extern "C" {
 #define SU3S_MATH_DEFAULT 0 /* the library default (see su3s_set_default_math)     */
 #define SU3S_MATH_F64 1     /* native IEEE FP64 with fused multiply-add              */
 #define SU3S_MATH_DF32 2    /* FP64-accurate pair-of-FP32 arithmetic (see below)     */
+#define SU3S_MATH_FX 3      /* FP64-accurate shared-exponent fixed point (see below) */
 
 typedef struct su3s_lattice su3s_lattice;
 typedef struct su3s_field su3s_field;
@@ -227,11 +228,24 @@ int su3s_eval(su3s_field* dest, const su3s_expr* e, void* stream);
  *                   Error per output <= ~2^-46 * sum_t |x_t y_t| (+ 2^-52 |z|);
  *                   needs every |input| and |intermediate| < 2^126, and values
  *                   below 2^-126 in magnitude may be flushed to zero.
- * Ignored for reduced-precision storage. */
+ *   SU3S_MATH_FX    the reals of each site object (matrix, vector, real)
+ *                   share the exponent of the object's largest element and
+ *                   become 53-bit signed integers; products are exact 32-bit
+ *                   integer multiply-adds into 64-bit accumulators (the
+ *                   lowest partial product is dropped), sums of terms with
+ *                   different scales are aligned by shifts, and each result
+ *                   is converted to FP64 once.  Error per output
+ *                   <= ~2^-47 * 6 * max|x| * max|y| over the two operand
+ *                   objects; objects whose largest magnitude is below 2^-958
+ *                   are flushed to zero; results must stay below 2^960 in
+ *                   magnitude, and results below 2^-1022 are returned with an
+ *                   absolute error below 2^-1022.
+ * Ignored for reduced-precision storage.  EINVAL for another value. */
 int su3s_eval_math(su3s_field* dest, const su3s_expr* e, int math, void* stream);
 
 /* Set the arithmetic SU3S_MATH_DEFAULT stands for (process-wide; initially
- * SU3S_MATH_DF32).  EINVAL for other values. */
+ * SU3S_MATH_DF32): SU3S_MATH_F64, SU3S_MATH_DF32 or SU3S_MATH_FX; EINVAL for
+ * other values. */
 int su3s_set_default_math(int math);
 
 /* Names of the compiled catalogue trees, one per line, into buf (truncated to

@@ -24,7 +24,7 @@ from . import build as _build
 MATRIX, VECTOR, REAL = 0, 1, 2
 F64, F32, BF16, F16, F64_C12, F32_C12 = 0, 1, 2, 3, 4, 5
 SOA, AOSOA = 0, 1
-MATH_DEFAULT, MATH_F64, MATH_DF32 = 0, 1, 2
+MATH_DEFAULT, MATH_F64, MATH_DF32, MATH_FX = 0, 1, 2, 3
 WIDTH = {MATRIX: 18, VECTOR: 6, REAL: 1}
 PREC_NAMES = {F64: "f64", F32: "f32", BF16: "bf16", F16: "f16", F64_C12: "f64_c12",
               F32_C12: "f32_c12"}

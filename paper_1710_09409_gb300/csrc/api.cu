@@ -98,6 +98,9 @@ void ensure_registered() {
     register_cat_lp();
     register_adj_f64();
     register_adj_df();
+    register_cat_fx();
+    register_cat_fx2();
+    register_adj_fx();
   });
 }
 
@@ -377,11 +380,16 @@ int canonicalize(const su3s_expr* e, Canon* out) {
 
 static int g_default_math = SU3S_MATH_DF32;
 
+bool valid_math(int math) {
+  return math == SU3S_MATH_DEFAULT || math == SU3S_MATH_F64 || math == SU3S_MATH_DF32 ||
+         math == SU3S_MATH_FX;
+}
+
 // Internal arithmetic id for a storage precision and a requested SU3S_MATH_*.
 int resolve_math(int prec, int math) {
   if (prec == SU3S_F64 || prec == SU3S_F64_C12) {
     int m = math == SU3S_MATH_DEFAULT ? g_default_math : math;
-    return m == SU3S_MATH_F64 ? MATH_F64 : MATH_DF;
+    return m == SU3S_MATH_F64 ? MATH_F64 : m == SU3S_MATH_FX ? MATH_FX : MATH_DF;
   }
   return MATH_F32;
 }
@@ -684,14 +692,13 @@ SU3S_EXPORT int su3s_eval(su3s_field* dest, const su3s_expr* e, void* stream) {
 }
 
 SU3S_EXPORT int su3s_eval_math(su3s_field* dest, const su3s_expr* e, int math, void* stream) {
-  if (math != SU3S_MATH_DEFAULT && math != SU3S_MATH_F64 && math != SU3S_MATH_DF32)
-    return fail(SU3S_EINVAL, "bad arithmetic %d", math);
+  if (!valid_math(math)) return fail(SU3S_EINVAL, "bad arithmetic %d", math);
   return do_eval(dest, e, math, (cudaStream_t)stream);
 }
 
 SU3S_EXPORT int su3s_set_default_math(int math) {
-  if (math != SU3S_MATH_F64 && math != SU3S_MATH_DF32)
-    return fail(SU3S_EINVAL, "default arithmetic must be SU3S_MATH_F64 or SU3S_MATH_DF32");
+  if (math == SU3S_MATH_DEFAULT || !valid_math(math))
+    return fail(SU3S_EINVAL, "default arithmetic must be SU3S_MATH_F64, SU3S_MATH_DF32 or SU3S_MATH_FX");
   g_default_math = math;
   return ok();
 }
@@ -701,7 +708,7 @@ SU3S_EXPORT int su3s_catalogue(char* buf, size_t cap) {
   ensure_registered();
   std::string out;
   static const char* pn[] = {"f64", "f32", "bf16", "f16", "f64_c12", "f32_c12"};
-  static const char* mn[] = {"", "f64", "df32", "f32"};
+  static const char* mn[] = {"", "f64", "df32", "f32", "fx"};
   for (auto& kv : eval_reg()) {
     out += "eval " + std::get<0>(kv.first) + " " + pn[std::get<1>(kv.first)] + " " +
            mn[std::get<2>(kv.first)] + "\n";
@@ -833,8 +840,7 @@ SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
         return fail(SU3S_ETYPE, "gradient %zu has the wrong kind", i);
     }
   }
-  if (math != SU3S_MATH_DEFAULT && math != SU3S_MATH_F64 && math != SU3S_MATH_DF32)
-    return fail(SU3S_EINVAL, "bad arithmetic %d", math);
+  if (!valid_math(math)) return fail(SU3S_EINVAL, "bad arithmetic %d", math);
   const int m = math_for(SU3S_F64, math);
   const EvalEntry* ent = find_adjoint(c.sig, m);
   if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled adjoint kernel for %s", c.sig.c_str());

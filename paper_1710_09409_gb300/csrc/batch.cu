@@ -126,7 +126,7 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     return fail(SU3S_EINVAL, "threads per block must be a multiple of 32 in 32..256");
   if (tile_sites == 0) tile_sites = 4 * threads;
   if (tile_sites < threads) return fail(SU3S_EINVAL, "tile smaller than a block");
-  if (math != SU3S_MATH_DEFAULT && math != SU3S_MATH_F64 && math != SU3S_MATH_DF32)
+  if (!valid_math(math))
     return fail(SU3S_EINVAL, "bad arithmetic %d", math);
   int m = resolve_math(SU3S_F64, math);
   (void)stream;
@@ -179,7 +179,9 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   }
 
   // persistent grid from occupancy
-  const void* kern = m == MATH_F64 ? (const void*)&k_batch<MathF64> : (const void*)&k_batch<MathDF>;
+  const void* kern = m == MATH_F64  ? (const void*)&k_batch<MathF64>
+                     : m == MATH_FX ? (const void*)&k_batch<MathFX>
+                                    : (const void*)&k_batch<MathDF>;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
   if (per_sm < 1) per_sm = 1;
@@ -198,6 +200,7 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   if (ce == cudaSuccess) {
     if (b->ntiles > 0) {
       if (m == MATH_F64) k_batch<MathF64><<<(unsigned)grid, threads, 0, cap>>>(b->d_items, b->d_tiles, b->ntiles);
+      else if (m == MATH_FX) k_batch<MathFX><<<(unsigned)grid, threads, 0, cap>>>(b->d_items, b->d_tiles, b->ntiles);
       else k_batch<MathDF><<<(unsigned)grid, threads, 0, cap>>>(b->d_items, b->d_tiles, b->ntiles);
       ce = cudaGetLastError();
       if (ce != cudaSuccess) rc = cuda_fail(ce, "persistent kernel capture");

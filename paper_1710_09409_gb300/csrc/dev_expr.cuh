@@ -202,6 +202,31 @@ template <class M, bool FIRST, int SG, bool AX, bool AY>
 __device__ __forceinline__ void mm_acc(typename M::A* z, const typename M::R* x,
                                        const typename M::R* y) {
   constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
+  if constexpr (M::kScaled) {
+    // integer multiply-adds have a long latency: advance the 18 independent
+    // accumulators together, one inner index j at a time
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          typename M::A& re = z[2 * (3 * i + k)];
+          typename M::A& im = z[2 * (3 * i + k) + 1];
+          const int xi = AX ? (3 * j + i) : (3 * i + j);
+          const int yi = AY ? (3 * k + j) : (3 * j + k);
+          if (FIRST && j == 0) {
+            M::template fma<true, SG>(re, x[2 * xi], y[2 * yi]);
+            M::template fma<true, SG * sy>(im, x[2 * xi], y[2 * yi + 1]);
+          } else {
+            M::template fma<false, SG>(re, x[2 * xi], y[2 * yi]);
+            M::template fma<false, SG * sy>(im, x[2 * xi], y[2 * yi + 1]);
+          }
+          M::template fma<false, -SG * sx * sy>(re, x[2 * xi + 1], y[2 * yi + 1]);
+          M::template fma<false, SG * sx>(im, x[2 * xi + 1], y[2 * yi]);
+        }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -336,8 +361,20 @@ __device__ __forceinline__ void vec_add(typename M::A* z, const typename M::R* x
 template <class M, int W, bool FIRST, int SG>
 __device__ __forceinline__ void vec_scale_add(typename M::A* z, const typename M::R& s,
                                               const typename M::R* x) {
+  if constexpr (M::kScaled && !FIRST) {
+    // the product s*x has its own scale: form it, then align and add
 #pragma unroll
-  for (int r = 0; r < W; ++r) M::template fma<FIRST, SG>(z[r], s, x[r]);
+    for (int r = 0; r < W; ++r) M::compact(z[r]);
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      typename M::A t;
+      M::template fma<true, 1>(t, s, x[r]);
+      M::template combine<SG>(z[r], t);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < W; ++r) M::template fma<FIRST, SG>(z[r], s, x[r]);
+  }
 }
 
 template <class M>
@@ -351,10 +388,16 @@ __device__ __forceinline__ void adjoint(typename M::R* z, const typename M::R* x
     }
 }
 
+// Accumulators of one object -> operand values (with a shared exponent for
+// the fixed-point arithmetic).
 template <class M, int W>
 __device__ __forceinline__ void finish(typename M::R* z, const typename M::A* a) {
+  if constexpr (M::kScaled) {
+    M::template finish_obj<W>(z, a);
+  } else {
 #pragma unroll
-  for (int r = 0; r < W; ++r) z[r] = M::finish(a[r]);
+    for (int r = 0; r < W; ++r) z[r] = M::finish(a[r]);
+  }
 }
 
 // ------------------------------------------------------------ forward
@@ -405,8 +448,16 @@ __device__ __forceinline__ void acc_into(const C& ctx, typename M::A* acc) {
   }
 }
 
+template <class M, int SG, class C, class X, class Y>
+__device__ __forceinline__ void mul_combine(const C& ctx, typename M::A* acc, Mul<X, Y>*);
+
 template <class M, bool FIRST, int SG, class C, class X, class Y>
 __device__ __forceinline__ void acc_node(const C& ctx, typename M::A* acc, Mul<X, Y>*) {
+  if constexpr (M::kScaled && !FIRST) {
+    // a product added to an accumulator of another scale
+    mul_combine<M, SG>(ctx, acc, (Mul<X, Y>*)nullptr);
+    return;
+  }
   using OX = Operand<X>;
   using OY = Operand<Y>;
   using BX = typename OX::base;
@@ -440,6 +491,10 @@ __device__ __forceinline__ void mul_combine(const C& ctx, typename M::A* acc, Mu
   using OY = Operand<Y>;
   using BX = typename OX::base;
   using BY = typename OY::base;
+  if constexpr (M::kScaled) {
+#pragma unroll
+    for (int r = 0; r < Width<Mul<X, Y>::kind>::value; ++r) M::compact(acc[r]);
+  }
   typename M::R xv[Width<BX::kind>::value];
   typename M::R yv[Width<BY::kind>::value];
   value<BX, M>(ctx, xv);
@@ -491,6 +546,9 @@ template <class M, int W, int I, bool ONCE, class GA, class Sink>
 __device__ __forceinline__ void emit_acc(const typename M::A* contrib, GA& ga, Sink& sink) {
   if constexpr (ONCE) {
     sink.template put<I, W>(contrib);
+  } else if constexpr (M::kScaled) {
+#pragma unroll
+    for (int r = 0; r < W; ++r) M::template combine<1>(ga.g[I][r], contrib[r]);
   } else {
 #pragma unroll
     for (int r = 0; r < W; ++r) {

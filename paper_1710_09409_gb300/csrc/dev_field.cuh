@@ -44,7 +44,8 @@ __device__ __forceinline__ double u2d(uint32_t lo, uint32_t hi) {
 
 // --------------------------------------------------------------- storages
 // Each storage moves one complex component of VPS consecutive sites with one
-// vector access.  Values are produced in the arithmetic of Math.
+// vector access.  Values are produced in the arithmetic of Math (FP64 storage:
+// Math::from_bits; an object is complete after Math::normalize_obj).
 
 template <int PREC>
 struct Store;
@@ -58,13 +59,8 @@ struct Store<P_F64> {
   __device__ static __forceinline__ void load(const void* base, int64_t e, typename M::R* re,
                                               typename M::R* im) {
     uint4 v = ld16((const char*)base + e * 16);
-    if constexpr (M::kNative64) {
-      re[0] = u2d(v.x, v.y);
-      im[0] = u2d(v.z, v.w);
-    } else {
-      re[0] = df_split_bits(v.x, v.y);
-      im[0] = df_split_bits(v.z, v.w);
-    }
+    re[0] = M::from_bits(v.x, v.y);
+    im[0] = M::from_bits(v.z, v.w);
   }
   // from accumulators
   template <class M>
@@ -158,13 +154,13 @@ struct BaseStore<P_F32_C12> {
   using type = Store<P_F32>;
 };
 
-// Real fields (FP64 only): one double per site object, VPS = 1.
+// Real fields (FP64 only): one double per site object, VPS = 1.  Values
+// come back as Math::from_bits; the caller normalises the object.
 struct StoreReal {
   template <class M>
   __device__ static __forceinline__ typename M::R load(const void* base, int64_t e) {
     uint2 v = ld8((const char*)base + e * 8);
-    if constexpr (M::kNative64) return u2d(v.x, v.y);
-    else return df_split_bits(v.x, v.y);
+    return M::from_bits(v.x, v.y);
   }
   template <class M>
   __device__ static __forceinline__ void store_acc(void* base, int64_t e, const typename M::A& a) {

@@ -30,6 +30,13 @@ struct IsC12 {
 // (c, j, k) cyclic.
 template <class M>
 __device__ __forceinline__ void rebuild_row2(typename M::R* m) {
+  // fixed point: row 2 comes out at the scale of a product; the 18 reals are
+  // renormalised together to one shared exponent
+  typename M::A a[M::kScaled ? 18 : 1];
+  if constexpr (M::kScaled) {
+#pragma unroll
+    for (int r = 0; r < 12; ++r) a[r] = M::to_acc(m[r]);
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int j = (c + 1) % 3, k = (c + 2) % 3;
@@ -47,9 +54,15 @@ __device__ __forceinline__ void rebuild_row2(typename M::R* m) {
     M::template fma<false, -1>(im, aji, bkr);
     M::template fma<false, 1>(im, akr, bji);
     M::template fma<false, 1>(im, aki, bjr);
-    m[12 + 2 * c] = M::finish(re);
-    m[12 + 2 * c + 1] = M::finish(im);
+    if constexpr (M::kScaled) {
+      a[12 + 2 * c] = re;
+      a[12 + 2 * c + 1] = im;
+    } else {
+      m[12 + 2 * c] = M::finish(re);
+      m[12 + 2 * c + 1] = M::finish(im);
+    }
   }
+  if constexpr (M::kScaled) M::template finish_obj<18>(m, a);
 }
 
 // Load leaf slot I (kind K) of VPS consecutive sites starting at site s.
@@ -59,6 +72,7 @@ __device__ __forceinline__ void load_obj(const FieldDesc& f, int64_t s, int mu, 
   if constexpr (K == KR) {
     static_assert(VPS == 1, "real fields are FP64");
     ctx[0].leaf[slot][0] = StoreReal::template load<M>(f.ptr, b);
+    M::template normalize_obj<1>(ctx[0].leaf[slot]);
   } else {
     using St = typename BaseStore<PREC>::type;
     constexpr int NC = (K == KV) ? 3 : (IsC12<PREC>::value ? 6 : 9);
@@ -71,6 +85,10 @@ __device__ __forceinline__ void load_obj(const FieldDesc& f, int64_t s, int mu, 
         ctx[v].leaf[slot][2 * c] = re[v];
         ctx[v].leaf[slot][2 * c + 1] = im[v];
       }
+    }
+    if constexpr (PREC == P_F64 || PREC == P_F64_C12) {
+#pragma unroll
+      for (int v = 0; v < VPS; ++v) M::template normalize_obj<2 * NC>(ctx[v].leaf[slot]);
     }
     if constexpr (K == KM && IsC12<PREC>::value) {
 #pragma unroll
@@ -329,21 +347,17 @@ template <int K, int PREC, class M, class C>
 __device__ __forceinline__ void read_obj(const unsigned char* src, int lane, C& ctx, int slot) {
   if constexpr (K == KR) {
     const uint2 v = reinterpret_cast<const uint2*>(src)[lane];
-    if constexpr (M::kNative64) ctx.leaf[slot][0] = u2d(v.x, v.y);
-    else ctx.leaf[slot][0] = df_split_bits(v.x, v.y);
+    ctx.leaf[slot][0] = M::from_bits(v.x, v.y);
+    M::template normalize_obj<1>(ctx.leaf[slot]);
   } else {
     constexpr int NC = StageBytes<K, PREC>::value / 512;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const uint4 v = reinterpret_cast<const uint4*>(src + c * 512)[lane];
-      if constexpr (M::kNative64) {
-        ctx.leaf[slot][2 * c] = u2d(v.x, v.y);
-        ctx.leaf[slot][2 * c + 1] = u2d(v.z, v.w);
-      } else {
-        ctx.leaf[slot][2 * c] = df_split_bits(v.x, v.y);
-        ctx.leaf[slot][2 * c + 1] = df_split_bits(v.z, v.w);
-      }
+      ctx.leaf[slot][2 * c] = M::from_bits(v.x, v.y);
+      ctx.leaf[slot][2 * c + 1] = M::from_bits(v.z, v.w);
     }
+    M::template normalize_obj<2 * NC>(ctx.leaf[slot]);
     if constexpr (K == KM && IsC12<PREC>::value) rebuild_row2<M>(ctx.leaf[slot]);
   }
 }

@@ -25,6 +25,28 @@
 //                scaled to units of the last place gives the low 29 bits.
 //            Error per output ~2^-46 * sum_t |x_t y_t| + 2^-52 |z|.  Needs all
 //            magnitudes below 2^126; magnitudes below 2^-126 may be flushed.
+//   MathFX   FP64-accurate arithmetic on the integer multiply-add units
+//            (shared-exponent fixed point):
+//              * the reals of one site object (a matrix, a vector, a real)
+//                share one exponent E, that of the object's largest element;
+//                each real becomes a signed integer m = x * 2^(1075-E) with
+//                |m| < 2^53 (the 53-bit significand shifted right by the
+//                element's exponent gap, truncated; negative values take the
+//                one's complement), held as m = h*2^25 + l;
+//              * a product term x*y is h_x*h_y (one 32x32->64-bit multiply-add)
+//                plus the cross terms h_x*l_y + l_x*h_y, whose high 32 bits
+//                are accumulated (two multiply-high-adds); l_x*l_y, below the
+//                accumulator's unit, is dropped.  Every term of one product
+//                shares the scale E_x + E_y, so a 3x3 complex product is 108
+//                exact integer multiply-adds into 64-bit accumulators;
+//              * sums of products with different scales are aligned by
+//                arithmetic shifts; an intermediate object is renormalised to
+//                a shared exponent; the result is converted with one
+//                int64 -> FP64 conversion and an exponent adjustment.
+//            Error per output <= ~2^-47 * 6 * max|x| * max|y| over the two
+//            operand objects (absolute, relative to the objects' largest
+//            elements).  Objects whose largest magnitude is below 2^-958 are
+//            flushed to zero; results must stay below 2^960 in magnitude.
 //   MathF32  FP32 arithmetic for FP32/BF16/FP16 storage (FP32 accumulation).
 #pragma once
 
@@ -82,7 +104,13 @@ struct MathF64 {
   using R = double;   // one real component
   using A = double;   // accumulator
   static constexpr bool kNative64 = true;
+  static constexpr bool kScaled = false;  // every term shares one scale
   __device__ static __forceinline__ R from_f64(double x) { return x; }
+  __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
+    return __hiloint2double((int)hi, (int)lo);
+  }
+  template <int W>
+  __device__ static __forceinline__ void normalize_obj(R*) {}
   __device__ static __forceinline__ double to_f64(const A& a) { return a; }
   __device__ static __forceinline__ R finish(const A& a) { return a; }
   __device__ static __forceinline__ A to_acc(const R& x) { return x; }
@@ -117,7 +145,13 @@ struct MathDF {
   using R = df;
   using A = DAcc;
   static constexpr bool kNative64 = false;
+  static constexpr bool kScaled = false;
   __device__ static __forceinline__ R from_f64(double x) { return df_split(x); }
+  __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
+    return df_split_bits(lo, hi);
+  }
+  template <int W>
+  __device__ static __forceinline__ void normalize_obj(R*) {}
   __device__ static __forceinline__ double to_f64(const A& a) { return df_to_double(a.S, a.lo); }
   __device__ static __forceinline__ R finish(const A& a) { return df_norm(a.S, a.lo); }
   __device__ static __forceinline__ A to_acc(const R& x) { return DAcc{x.h, x.l}; }
@@ -189,11 +223,167 @@ struct MathDF {
   }
 };
 
+// -------------------------------------------------------------- MathFX
+// One real of an object: value (h * 2^25 + l * 2^-6) * 2^(e - 1075), with
+// |h| <= 2^28, |l| < 2^31 and l a multiple of 64 (the low 25 bits of m,
+// pre-shifted for the multiply-high of the cross terms).  e is the object's
+// shared exponent; before normalize_obj, (h, l) hold the raw FP64 bits.
+struct fxr {
+  int h, l, e;
+};
+// Accumulator: value (hh + 2 * cr) * 2^(e - 2100).
+struct FAcc {
+  long long hh;
+  int cr, e;
+};
+
+constexpr int kFxEmin = 64;         // biased exponent floor of an object
+constexpr int kFxZeroE = -(1 << 20);  // scale of an empty accumulator
+
+// Shifts with PTX semantics: amounts beyond 63 give 0 (logical) or the sign
+// (arithmetic).
+__device__ __forceinline__ uint64_t fx_shr(uint64_t x, uint32_t s) {
+  uint64_t r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+}
+__device__ __forceinline__ long long fx_sar(long long x, uint32_t s) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+}
+__device__ __forceinline__ long long fx_total(const FAcc& a) {
+  return a.hh + ((long long)a.cr << 1);
+}
+
+struct MathFX {
+  using R = fxr;
+  using A = FAcc;
+  static constexpr bool kNative64 = false;
+  static constexpr bool kScaled = true;  // terms of different objects differ in scale
+
+  __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
+    return fxr{(int)hi, (int)lo, 0};
+  }
+  // Raw FP64 bits of W reals -> shared-exponent fixed point.
+  template <int W>
+  __device__ static __forceinline__ void normalize_obj(R* x) {
+    uint32_t amax = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) amax = max(amax, (uint32_t)x[i].h & 0x7FFFFFFFu);
+    const int E = max((int)(amax >> 20), kFxEmin);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const uint32_t hi = (uint32_t)x[i].h, lo = (uint32_t)x[i].l;
+      const uint32_t ah = hi & 0x7FFFFFFFu;
+      // zero and subnormal elements have exponent 0: their gap is >= 64
+      const uint32_t d = (uint32_t)(E - (int)(ah >> 20));
+      const uint64_t M = ((uint64_t)((ah & 0xFFFFFu) | 0x100000u) << 32) | lo;
+      const uint64_t m = fx_shr(M, d);
+      const uint32_t sg = (uint32_t)((int)hi >> 31);
+      x[i].h = (int)((uint32_t)(m >> 25) ^ sg);
+      x[i].l = (int)((((uint32_t)m << 6) ^ sg) & 0x7FFFFFC0u);
+      x[i].e = E;
+    }
+  }
+  // W accumulators (scales may differ) -> one object with a shared exponent.
+  template <int W>
+  __device__ static __forceinline__ void finish_obj(R* out, const A* a) {
+    int e = a[0].e;
+#pragma unroll
+    for (int i = 1; i < W; ++i) e = max(e, a[i].e);
+    long long T[W];
+    uint64_t orv = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      T[i] = fx_sar(fx_total(a[i]), (uint32_t)(e - a[i].e));
+      orv |= (uint64_t)(T[i] ^ (T[i] >> 63));
+    }
+    const int sh = max(64 - __clzll((long long)orv) - 53, 0);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const long long m = fx_sar(T[i], (uint32_t)sh);
+      out[i].h = (int)(m >> 25);
+      out[i].l = (int)(((uint32_t)m << 6) & 0x7FFFFFC0u);
+      out[i].e = e + sh - 1025;
+    }
+  }
+  // Result: T = hh + 2 cr converted once (round to nearest even), then the
+  // exponent field moved by the accumulator's scale.  Supported range: results
+  // below 2^960 in magnitude; results below 2^-1022 come out as subnormals of
+  // unspecified significand (absolute error below 2^-1022).
+  __device__ static __forceinline__ double to_f64(const A& a) {
+    const double d = __ll2double_rn(fx_total(a));
+    const uint32_t hi = (uint32_t)__double2hiint(d);
+    const int ah = (int)(hi & 0x7FFFFFFFu);
+    // d == 0 or its biased exponent is in [1023, 1085] (|T| < 2^62): with the
+    // adjustment clamped to [-1100, 960] the new exponent stays below 2047
+    const int k = min(max(a.e - 2100, -1100), 960) * (1 << 20);
+    const int nh = max(ah + k * min(ah, 1), 0);
+    return __hiloint2double((int)((uint32_t)nh | (hi & 0x80000000u)), __double2loint(d));
+  }
+  __device__ static __forceinline__ R finish(const A& a) {
+    R r;
+    finish_obj<1>(&r, &a);
+    return r;
+  }
+  __device__ static __forceinline__ A to_acc(const R& x) {
+    return FAcc{(long long)x.h * (1LL << 25) + (long long)(x.l >> 6), 0, x.e + 1025};
+  }
+  __device__ static __forceinline__ A zero() { return FAcc{0, 0, kFxZeroE}; }
+  __device__ static __forceinline__ R neg(const R& x) { return fxr{-x.h, -x.l, x.e}; }
+  __device__ static __forceinline__ R scalar(double s, float, float) {
+    R r = from_bits((uint32_t)__double2loint(s), (uint32_t)__double2hiint(s));
+    normalize_obj<1>(&r);
+    return r;
+  }
+
+  // a (+)= SG * x * y.  Not FIRST: a's scale must be x.e + y.e (terms of one
+  // product); terms of other scales go through combine.
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void fma(A& a, const R& x, const R& y) {
+    const int xh = SG > 0 ? x.h : -x.h;
+    const int xl = SG > 0 ? x.l : -x.l;
+    if (FIRST) {
+      a.hh = (long long)xh * y.h;
+      a.cr = __mulhi(xh, y.l) + __mulhi(xl, y.h);
+      a.e = x.e + y.e;
+    } else {
+      a.hh += (long long)xh * y.h;
+      a.cr += __mulhi(xh, y.l);
+      a.cr += __mulhi(xl, y.h);
+    }
+  }
+  // fold the cross-term sum into the 64-bit part (frees a register per
+  // accumulator that is no longer multiplied into)
+  __device__ static __forceinline__ void compact(A& a) {
+    a.hh = fx_total(a);
+    a.cr = 0;
+  }
+  // a += SG * b at the larger of the two scales
+  template <int SG>
+  __device__ static __forceinline__ void combine(A& a, const A& b) {
+    const int e = max(a.e, b.e);
+    const long long ta = fx_sar(fx_total(a), (uint32_t)(e - a.e));
+    const long long tb = fx_sar(fx_total(b), (uint32_t)(e - b.e));
+    a.hh = SG > 0 ? ta + tb : ta - tb;
+    a.cr = 0;
+    a.e = e;
+  }
+  template <bool FIRST, int SG>
+  __device__ static __forceinline__ void add(A& a, const R& x) {
+    const A t = to_acc(SG > 0 ? x : neg(x));
+    if (FIRST) a = t;
+    else combine<1>(a, t);
+  }
+};
+
 // ------------------------------------------------------------- MathF32
 struct MathF32 {
   using R = float;
   using A = float;
   static constexpr bool kNative64 = false;
+  static constexpr bool kScaled = false;
   __device__ static __forceinline__ R finish(const A& a) { return a; }
   __device__ static __forceinline__ A to_acc(const R& x) { return x; }
   __device__ static __forceinline__ A zero() { return 0.0f; }

@@ -91,6 +91,7 @@ bool tma_layout_ok(const su3s_field* f);
 int build_params(const Canon& c, const su3s_field* dest, int vps, KParams* p);
 
 // arithmetic resolution for a storage precision
+bool valid_math(int math);
 int resolve_math(int prec, int math);
 
 // interpreter
@@ -111,5 +112,8 @@ void register_cat_df2();
 void register_cat_lp();
 void register_adj_f64();
 void register_adj_df();
+void register_cat_fx();
+void register_cat_fx2();
+void register_adj_fx();
 
 }  // namespace su3s

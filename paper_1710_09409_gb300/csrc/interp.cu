@@ -39,6 +39,7 @@ __device__ __forceinline__ void i_load(const FieldDesc& f, int kind, int64_t s, 
   const int64_t b = elem_base(f, s, mu);
   if (kind == KR) {
     r[0] = StoreReal::template load<M>(f.ptr, b);
+    M::template normalize_obj<1>(r);
     return;
   }
   const int nc = kind == KM ? 9 : 3;
@@ -47,6 +48,20 @@ __device__ __forceinline__ void i_load(const FieldDesc& f, int kind, int64_t s, 
     Store<P_F64>::template load<M>(f.ptr, b + c * f.s_c, re, im);
     r[2 * c] = re[0];
     r[2 * c + 1] = im[0];
+  }
+  if (kind == KM) M::template normalize_obj<18>(r);
+  else M::template normalize_obj<6>(r);
+}
+
+// Accumulators of an object of w reals -> register values.
+template <class M>
+__device__ __forceinline__ void i_finish(typename M::R* d, const typename M::A* acc, int w) {
+  if constexpr (M::kScaled) {
+    if (w == 18) M::template finish_obj<18>(d, acc);
+    else if (w == 6) M::template finish_obj<6>(d, acc);
+    else M::template finish_obj<1>(d, acc);
+  } else {
+    for (int r = 0; r < w; ++r) d[r] = M::finish(acc[r]);
   }
 }
 
@@ -94,7 +109,7 @@ __global__ void __launch_bounds__(256) k_interp(const __grid_constant__ KParams 
           continue;
         }
       }
-      for (int r = 0; r < in.w; ++r) d[r] = M::finish(acc[r]);
+      i_finish<M>(d, acc, in.w);
     }
     const R* z = reg[prog.root];
     const int64_t b = elem_base(p.dst, s, mu);
@@ -205,10 +220,13 @@ int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, 
   bld.prog.root_kind = c.kind;
   KParams p;
   build_params(c, dest, 1, &p);
-  const void* kern = math == MATH_F64 ? (const void*)&k_interp<MathF64> : (const void*)&k_interp<MathDF>;
+  const void* kern = math == MATH_F64  ? (const void*)&k_interp<MathF64>
+                     : math == MATH_FX ? (const void*)&k_interp<MathFX>
+                                       : (const void*)&k_interp<MathDF>;
   dim3 grid, block;
   launch_geometry(kern, p.nvec, p.nmu, &grid, &block);
   if (math == MATH_F64) k_interp<MathF64><<<grid, block, 0, st>>>(p, bld.prog);
+  else if (math == MATH_FX) k_interp<MathFX><<<grid, block, 0, st>>>(p, bld.prog);
   else k_interp<MathDF><<<grid, block, 0, st>>>(p, bld.prog);
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "interpreter kernel launch");

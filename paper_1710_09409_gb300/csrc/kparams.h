@@ -7,7 +7,7 @@ namespace su3s {
 
 enum Prec { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_F16 = 3, P_F64_C12 = 4, P_F32_C12 = 5 };
 enum Kind { K_MATRIX = 0, K_VECTOR = 1, K_REAL = 2 };
-enum MathId { MATH_F64 = 1, MATH_DF = 2, MATH_F32 = 3 };
+enum MathId { MATH_F64 = 1, MATH_DF = 2, MATH_F32 = 3, MATH_FX = 4 };
 
 constexpr int kMaxLeaves = 6;
 constexpr int kMaxScalars = 4;

@@ -177,7 +177,7 @@ def test_canonical_signatures(L):
 
 def test_catalogue_covers_hot_path_rows(L):
     cat = set(su3s.catalogue())
-    for math in ("f64", "df32"):
+    for math in ("f64", "df32", "fx"):
         for sig in ("mul(M0,M1)", "mul(M0,V1)", "add(mul(M0,M1),mul(M2,M3))",
                     "add(mul(mul(M0,M1),M2),scale(s0,M3))", "sub(mul(adj(M0),M1),mul(M1,adj(M0)))",
                     "add(add(R0,R1),mul(R0,R1))"):
@@ -187,6 +187,7 @@ def test_catalogue_covers_hot_path_rows(L):
     for p in ("f32", "bf16", "f16"):
         assert ("eval", "mul(M0,M1)", p, "f32") in cat
     assert ("eval", "mul(M0,M1)", "f64_c12", "df32") in cat
+    assert ("eval", "mul(M0,M1)", "f64_c12", "fx") in cat
     assert ("eval", "mul(M0,M1)", "f64_c12", "f64") in cat
     assert ("eval", "mul(M0,M1)", "f32_c12", "f32") in cat
 
@@ -213,6 +214,8 @@ def test_eval_validation_before_any_launch(L):
         _, acc = t.op("add", acc, h)
     assert L.su3s_eval_math(t.field(), acc, 0, None) == 6            # too many leaves
     assert L.su3s_set_default_math(5) == 1
+    assert L.su3s_set_default_math(0) == 1
+    assert L.su3s_set_default_math(su3s.MATH_FX) == 0
     assert L.su3s_set_default_math(su3s.MATH_DF32) == 0
 
 

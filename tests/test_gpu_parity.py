@@ -1,7 +1,7 @@
 """Parity of the CUDA path with the CPU oracle, through the C ABI.
 
 Tolerances:
-  * FP64 storage (native FP64 or pair-of-FP32 arithmetic): 1e-13 per real
+  * FP64 storage (native FP64, pair-of-FP32 or fixed-point arithmetic): 1e-13 per real
     component for products of SU(3) matrices (sum_t |x_t y_t| <= 1 there); for
     Gaussian operands the same bound scaled by max(1, sum_t |x_t y_t|).
   * FP32/BF16/FP16 storage with FP32 accumulation: against the oracle that
@@ -21,6 +21,9 @@ pytestmark = pytest.mark.gpu
 
 SEED = synth.SEED_BASE
 TOL = 1e-13
+# arithmetics for FP64 storage: native FP64, pair of FP32, shared-exponent fixed point
+MATHS = [1, 2, 3]
+MATH_IDS = ["f64", "df32", "fx"]
 DIMS = [(1, 1, 1, 1), (2, 2, 2, 2), (3, 2, 1, 5), (6, 5, 7, 3), (8, 8, 8, 8)]
 LAYOUTS = [("soa", 0, 0), ("aosoa4", 1, 4), ("aosoa32", 1, 32), ("aosoa128", 1, 128)]
 
@@ -58,7 +61,7 @@ def tree_expr(tree, fields):
 
 
 # ------------------------------------------------------------------ products
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("lay", LAYOUTS, ids=layout_id)
 @pytest.mark.parametrize("dims", DIMS, ids=str)
 def test_mm(su3s, dims, lay, math):
@@ -72,7 +75,7 @@ def test_mm(su3s, dims, lay, math):
     assert err < TOL
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("lay", LAYOUTS[:2], ids=layout_id)
 @pytest.mark.parametrize("dims", [(3, 2, 1, 5), (8, 8, 8, 8)], ids=str)
 def test_mv(su3s, dims, lay, math):
@@ -87,7 +90,7 @@ def test_mv(su3s, dims, lay, math):
     assert np.abs(z.download() - ref).max() < TOL * scale
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2]], ids=layout_id)
 def test_lorentz_links(su3s, lay, math):
     dims = (6, 5, 7, 3)
@@ -100,7 +103,7 @@ def test_lorentz_links(su3s, lay, math):
     assert np.abs(z.download() - oracle.mm(f["a"], f["b"])).max() < TOL
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_gaussian_operands(su3s, math):
     dims = (6, 5, 7, 3)
     v = synth.volume(dims)
@@ -130,13 +133,13 @@ def test_zero_and_identity_inputs(su3s):
     eye = np.zeros((v, 3, 3, 2))
     eye[:, [0, 1, 2], [0, 1, 2], 0] = 1.0
     f = lattice_fields(dims, SEED)
-    for math in (1, 2):
+    for math in MATHS:
         a, i = upload(su3s, lat, f["a"]), upload(su3s, lat, eye)
         z = a.like()
         su3s.evaluate(z, a * i, math)
         if math == 1:   # native FP64: multiplying by the identity is exact
             assert np.array_equal(z.download() + 0.0, f["a"] + 0.0)
-        else:           # pair arithmetic carries ~48 significant bits
+        else:           # pair arithmetic and fixed point carry >= 48 significant bits
             assert np.abs(z.download() - f["a"]).max() <= 2.0 ** -46
         zero = upload(su3s, lat, np.zeros_like(eye))
         su3s.evaluate(z, a * zero, math)
@@ -144,7 +147,7 @@ def test_zero_and_identity_inputs(su3s):
 
 
 # -------------------------------------------------------------- fused trees
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("name,tree", [("E1", E1), ("E2", E2), ("E3", E3)], ids=["E1", "E2", "E3"])
 @pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2]], ids=layout_id)
 def test_fused_trees(su3s, name, tree, lay, math):
@@ -161,7 +164,7 @@ def test_fused_trees(su3s, name, tree, lay, math):
     assert np.abs(z.download() - ref).max() < TOL * 2
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_fused_equals_term_by_term_on_gpu(su3s, math):
     dims = (8, 8, 8, 8)
     lat = su3s.Lattice(dims)
@@ -178,7 +181,7 @@ def test_fused_equals_term_by_term_on_gpu(su3s, math):
     assert np.abs(fused.download() - tot.download()).max() < tol
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_interpreter_for_uncatalogued_trees(su3s, math):
     dims = (6, 5, 7, 3)
     lat = su3s.Lattice(dims)
@@ -212,7 +215,7 @@ def test_listing2_real_fields(su3s):
     dims = (6, 5, 7, 3)
     v = synth.volume(dims)
     lat = su3s.Lattice(dims)
-    for math in (1, 2):
+    for math in MATHS:
         for v1, v2, expr, v3 in rows:
             f1 = upload(su3s, lat, np.full(v, float(v1)), kind=su3s.REAL)
             f2 = upload(su3s, lat, np.full(v, float(v2)), kind=su3s.REAL)
@@ -230,7 +233,7 @@ def test_real_field_trees_random(su3s):
     a, b = upload(su3s, lat, r1, kind=su3s.REAL), upload(su3s, lat, r2, kind=su3s.REAL)
     tree = ("add", ("add", ("leaf", "x"), ("leaf", "y")), ("mul", ("leaf", "x"), ("leaf", "y")))
     ref = oracle.eval_tree(tree, {"x": r1, "y": r2})
-    for math in (1, 2):
+    for math in MATHS:
         z = a.like()
         su3s.evaluate(z, a + b + a * b, math)
         assert np.abs(z.download() - ref).max() < TOL
@@ -279,7 +282,7 @@ def test_reduced_precision_mv(su3s, fmt):
 
 
 # ------------------------------------------------------------- two-row SU(3)
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2]], ids=layout_id)
 def test_c12_f64(su3s, lay, math):
     dims = (6, 5, 7, 3)
@@ -344,7 +347,7 @@ def test_pack_zeroes_pad_sites(su3s):
 
 
 # ---------------------------------------------------------- reverse mode
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("name,tree", [("MM", ("mul", ("leaf", "a"), ("leaf", "b"))), ("E1", E1),
                                        ("E2", E2), ("E3", E3)], ids=["MM", "E1", "E2", "E3"])
 def test_adjoint_kernels(su3s, name, tree, math):
@@ -362,7 +365,7 @@ def test_adjoint_kernels(su3s, name, tree, math):
         assert np.abs(g.download() - ref[n]).max() < TOL * wscale, n
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_adjoint_matrix_vector(su3s, math):
     dims = (6, 5, 7, 3)
     lat = su3s.Lattice(dims)
@@ -420,7 +423,7 @@ def test_autograd_gradient_16x4(su3s):
             assert abs(fd - grad.reshape(-1)[k]) < 1e-7 * max(1.0, abs(lo)) ** 0.5
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_autograd_fused_tree(su3s, math):
     dims = (6, 5, 7, 3)
     lat = su3s.Lattice(dims)
@@ -443,7 +446,7 @@ def config4_volumes(seed, n=64):
     return [shapes[min(int(p), len(shapes) - 1)] for p in picks]
 
 
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_batch_matches_separate_evaluations(su3s, math):
     seed = synth.SEED_BASE + 4
     shapes = config4_volumes(seed, 12)
@@ -480,7 +483,7 @@ def test_batch_matches_separate_evaluations(su3s, math):
 
 
 # --------------------------------------------- staged vs plain data movement
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2], LAYOUTS[3]], ids=layout_id)
 def test_tma_staging_is_bitwise_identical(su3s, lay, math):
     """The TMA-staged kernels (bulk copies into shared memory, one 32-site tile
@@ -528,7 +531,7 @@ def test_launch_geometry_does_not_change_results(su3s):
     F = {n: upload(su3s, lat, f[n]) for n in "abcd"}
     e = F["a"] * F["b"] + F["c"] * F["d"]
     outs = []
-    for math in (1, 2):
+    for math in MATHS:
         ref = None
         for th, bps in ((64, 0), (128, 2), (256, 0), (256, 8), (96, 1)):
             z = F["a"].like()
@@ -577,7 +580,7 @@ def test_reunitarize(su3s, prec, fmt, tol):
 
 
 # ------------------------------------------------------ full-size sampling
-@pytest.mark.parametrize("math", [1, 2], ids=["f64", "df32"])
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_full_size_48_sampled(su3s, math):
     """The 48^4 configuration in the launch geometry the benchmark uses:
     z=a*b, z=a*v and Lorentz z_mu=a_mu*b_mu checked on sampled sites."""
