@@ -8,6 +8,8 @@ volume-sweep configuration (5,308,416 sites):
   A7 z=a*b in two-row (12-real) SU(3) storage, FP64 and FP32,
   A8 64 lattices of mixed volumes, z=a*b+c*d each, one CUDA-graph launch,
   A9 reverse mode of z=a*b and of z=a*b+c*d.
+Before timing, the library's autotuner picks each row's launch shape and data
+movement (setup, outside the timed region; --no-tune keeps the defaults).
 `value` is the aggregate algorithmic bandwidth of the step (STREAM
 convention: every input read once, every output written once) with inputs
 resident in HBM; every field is larger than the 129 MB L2, so no flush is
@@ -163,6 +165,7 @@ class Row:
         self.name, self.nbytes, self.sites, self.run = name, nbytes, sites, run
         self.inputs, self.outputs, self.launches, self.dtype = inputs, outputs, launches, dtype
         self.ms = []
+        self.tune = None   # callable(stream) -> (threads, blocks/SM, variant, ms), forward rows
 
 
 def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True):
@@ -234,8 +237,11 @@ def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True)
         def run(stream, dest=dest, expr=expr):
             su3s.evaluate(dest, expr, su3s.MATH_DEFAULT, stream)
             return 1
-        return Row(name, bps * v * dest.nmu, v * dest.nmu, run, ins, [(dest, out_pin(dest))],
-                   dtype=dtype)
+        r = Row(name, bps * v * dest.nmu, v * dest.nmu, run, ins, [(dest, out_pin(dest))],
+                dtype=dtype)
+        r.tune = lambda stream, dest=dest, expr=expr: su3s.tune(dest, expr, su3s.MATH_DEFAULT,
+                                                                 stream)
+        return r
 
     if want("A2 z=a*b"):
         z = Fd["a"].like()
@@ -315,6 +321,8 @@ def _adjoint_rows(su3s, rows, want, v, Fd, Fw, P, out_pin):
         rows.append(Row(ROW_A9A, B_ADJ_MM * v, v, run_adj,
                         [(a, P["a"]), (b, P["b"]), (Fw, P["w"])],
                         [(ga, out_pin(ga)), (gb, out_pin(gb))]))
+        rows[-1].tune = lambda stream, a=a, b=b, ga=ga, gb=gb: su3s.tune_adjoint(
+            a * b, Fw, [ga, gb], su3s.MATH_DEFAULT, stream)
     if want(ROW_A9B):
         a, b, c, d = (Fd[n] for n in "abcd")
         g4 = [a.like() for _ in range(4)]
@@ -326,6 +334,8 @@ def _adjoint_rows(su3s, rows, want, v, Fd, Fw, P, out_pin):
         rows.append(Row(ROW_A9B, B_ADJ_E1 * v, v, run_adj1,
                         [(Fd[n], P[n]) for n in "abcd"] + [(Fw, P["w"])],
                         [(g, out_pin(g)) for g in g4]))
+        rows[-1].tune = lambda stream, e1=e1, g4=g4: su3s.tune_adjoint(
+            e1, Fw, g4, su3s.MATH_DEFAULT, stream)
     return rows
 
 
@@ -674,6 +684,9 @@ def main():
     ap.add_argument("--math", default="df32", choices=["fx", "df32", "f64"],
                     help="arithmetic of the FP64-storage rows in the step (the others are "
                          "timed beside it)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the library's autotuner (by default it picks each row's launch "
+                         "shape and data movement during setup, outside the timed region)")
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "tma", "tma_leaf"],
                     help="data movement of FP64-storage kernels (default: the library's choice)")
     args = ap.parse_args()
@@ -728,6 +741,14 @@ def main():
     with_host = not args.no_e2e
     rows, keep = build_rows(su3s, synth, torch, with_host, dims, want)
     torch.cuda.synchronize()
+    tuned = []
+    if not args.no_tune:
+        for r in rows:
+            if r.tune is not None:
+                th, bps, var, tms = r.tune(stream)
+                tuned.append({"row": r.name, "threads": th, "blocks_per_sm": bps,
+                              "variant": var, "ms": round(tms, 5)})
+        torch.cuda.synchronize()
 
     # device-resident timing
     sampler = ClockSampler(local)
@@ -800,10 +821,11 @@ def main():
                                     if full else "subset %s on %s" % (args.rows or "all rows",
                                                                       "x".join(map(str, dims)))),
                        "lattice": list(dims), "layout": "soa", "pipeline": args.pipeline,
+                       "tuned": not args.no_tune,
                        "l2": "every field larger than the 129 MB L2; no flush needed",
                        "bytes_per_step": bytes_step, "seed": SEED},
             "sites_per_s": round(a2["Gsites_s"] * 1e9 * ws, 0),
-            "rows": row_out, "other_arithmetic_rows": variants,
+            "rows": row_out, "other_arithmetic_rows": variants, "tuned": tuned,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
         }

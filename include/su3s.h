@@ -284,7 +284,7 @@ int su3s_device_error(int* code, void* stream);
  * grid-stride grids) with CUDA events on `stream` (synchronising it; dest is
  * overwritten), keeps the fastest for later su3s_eval calls and reports it in
  * *threads, *blocks_per_sm, *variant and its time in *best_ms (any may be
- * NULL). */
+ * NULL).  Not to be called while `stream` is being captured. */
 int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream, int* threads,
               int* blocks_per_sm, int* variant, float* best_ms);
 
@@ -326,6 +326,14 @@ int su3s_batch_destroy(su3s_batch* b);
  * once.  FP64 storage only; catalogue trees only (EUNSUPPORTED otherwise). */
 int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* grad_out, su3s_field* const* grad_leaves,
                       int nleaves, int math, void* stream);
+
+/* Autotune the reverse-mode kernel of `e` as su3s_tune does the forward one:
+ * arguments as for su3s_eval_adjoint (grad_leaves are overwritten while
+ * timing), result as for su3s_tune; later su3s_eval_adjoint calls on fields
+ * of this shape use the fastest geometry. */
+int su3s_tune_adjoint(const su3s_expr* e, const su3s_field* grad_out, su3s_field* const* grad_leaves,
+                      int nleaves, int math, void* stream, int* threads, int* blocks_per_sm,
+                      int* variant, float* best_ms);
 
 /* Number of unique leaves of `e` in *n. */
 int su3s_expr_num_leaves(const su3s_expr* e, int* n);

@@ -96,6 +96,8 @@ def load(build_if_missing=False):
         "su3s_batch_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64)], I),
         "su3s_batch_destroy": ([P], I),
         "su3s_eval_adjoint": ([P, P, PP, I, I, P], I),
+        "su3s_tune_adjoint": ([P, P, PP, I, I, P, ctypes.POINTER(I), ctypes.POINTER(I),
+                               ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)], I),
         "su3s_field_redot": ([P, P, P, P], I),
         "su3s_reunitarize": ([P, P, P], I),
     }
@@ -401,6 +403,19 @@ def eval_adjoint(expr, grad_out, grads, math=MATH_DEFAULT, stream=None):
     expr = _as_expr(expr)
     arr = (ctypes.c_void_p * max(1, len(grads)))(*[(g._h if g is not None else None) for g in grads])
     _check(_lib.su3s_eval_adjoint(expr._h, grad_out._h, arr, len(grads), math, _stream(stream)))
+
+
+def tune_adjoint(expr, grad_out, grads, math=MATH_DEFAULT, stream=None):
+    """Autotune the reverse-mode kernel of `expr` (arguments as for
+    eval_adjoint; `grads` are overwritten); returns (threads, blocks_per_sm,
+    variant, ms)."""
+    expr = _as_expr(expr)
+    arr = (ctypes.c_void_p * max(1, len(grads)))(*[(g._h if g is not None else None) for g in grads])
+    t, b, v, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(_lib.su3s_tune_adjoint(expr._h, grad_out._h, arr, len(grads), math, _stream(stream),
+                                  ctypes.byref(t), ctypes.byref(b), ctypes.byref(v),
+                                  ctypes.byref(ms)))
+    return t.value, b.value, v.value, ms.value
 
 
 def redot(x, y, out=None, stream=None):

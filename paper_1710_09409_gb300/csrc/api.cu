@@ -77,6 +77,8 @@ static EvalEntry make_entry(const Variants& v, int vps) {
   }
   e.vps = vps;
   e.default_variant = v.fn[1] ? v.default_variant : 0;
+  e.default_threads = v.default_threads;
+  e.default_bps = v.default_bps;
   return e;
 }
 
@@ -171,7 +173,16 @@ static int staged_occupancy(const void* kernel, int threads, int warp_bytes) {
 
 int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* out) {
   Geo g{0, 0, g_pipeline_pref};
-  find_geometry(e->kernel[0], nvec, nmu, &g);
+  const bool set = find_geometry(e->kernel[0], nvec, nmu, &g);
+  if (!set) {
+    // the tree's default launch; a pipeline preference overrides its variant
+    g.threads = e->default_threads;
+    g.bps = e->default_bps;
+    if (g_pipeline_pref >= 0 && g_pipeline_pref != e->default_variant) {
+      g.threads = 0;
+      g.bps = 0;
+    }
+  }
   const bool can_stage = e->fn[1] && tma_ok && nvec % 32 == 0;
   int variant = g.variant;
   if (variant < 0 || variant >= kNumVariants || !e->fn[variant]) variant = e->default_variant;
@@ -194,13 +205,20 @@ int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* 
   }
   out->fn = e->fn[0];
   out->variant = 0;
-  launch_geometry(e->kernel[0], nvec, nmu, &out->grid, &out->block);
+  plain_geometry(g.threads, g.bps, nvec, nmu, &out->grid, &out->block);
   return SU3S_OK;
 }
 
 void launch_geometry(const void* kernel, int64_t nvec, int nmu, dim3* grid, dim3* block) {
   Geo g{256, 0, -1};
   find_geometry(kernel, nvec, nmu, &g);
+  plain_geometry(g.threads, g.bps, nvec, nmu, grid, block);
+}
+
+// Plain-load grid: `threads` per block (0: 256); bps > 0 gives a grid-stride
+// grid of bps blocks per SM, else one site vector per thread.
+void plain_geometry(int threads, int bps, int64_t nvec, int nmu, dim3* grid, dim3* block) {
+  Geo g{threads, bps, -1};
   if (g.threads <= 0) g.threads = 256;
   int64_t nb;
   if (g.bps > 0) {
@@ -733,70 +751,80 @@ SU3S_EXPORT int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int 
   return ok();
 }
 
-SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream,
-                          int* threads_out, int* bps_out, int* variant_out, float* best_ms) {
-  Canon c;
-  int rc = check_eval(dest, e, &c);
-  if (rc) return rc;
-  const int m = math_for(dest->prec, math);
-  const EvalEntry* ent = find_eval(c.sig, dest->prec, m);
-  if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s", c.sig.c_str());
-  cudaStream_t st = (cudaStream_t)stream;
-  KParams p;
-  build_params(c, dest, ent->vps, &p);
+// Time every (variant, threads, blocks/SM) candidate of one registry entry on
+// the caller's fields and keep the fastest as the geometry of (kernel, shape).
+static int tune_entry(const EvalEntry* ent, const void* params, int64_t nvec, int nmu, bool tma_ok,
+                      cudaStream_t st, int* threads_out, int* bps_out, int* variant_out,
+                      float* best_ms) {
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(SU3S_ECUDA, "event creation failed");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
     return fail(SU3S_ECUDA, "event creation failed");
+  }
   const int th_c[] = {64, 128, 256};
-  const int bps_c[] = {0, 2, 4, 8, 16};
-  const bool tma = ent->fn[1] && tma_layout_ok(dest) && p.nvec % 32 == 0;
+  const int bps_c[] = {0, 2, 4, 8};
+  const bool tma = ent->fn[1] && tma_ok && nvec % 32 == 0;
   float best = 1e30f;
   int bt = 256, bb = 0, bv = 0;
-  struct Cand {
-    int var, th, bps;
-  };
-  std::vector<Cand> cands;
-  for (int var = 0; var < (tma ? kNumVariants : 1); ++var)
-    for (int th : th_c)
-      for (int bps : bps_c) cands.push_back(Cand{var, th, bps});
-  for (const Cand& cd : cands) {
-        const int var = cd.var, th = cd.th, bps = cd.bps;
-        set_geometry(ent->kernel[0], p.nvec, p.nmu, th, bps, var);
+  int rc = SU3S_OK;
+  for (int var = 0; var < (tma ? kNumVariants : 1) && rc == SU3S_OK; ++var) {
+    if (!ent->fn[var]) continue;
+    for (int th : th_c) {
+      if (var == 2 && th > 128) continue;  // per-leaf kernels take at most 4 warps
+      for (int bps : bps_c) {
+        set_geometry(ent->kernel[0], nvec, nmu, th, bps, var);
         Launch L;
-        plan_launch(ent, p.nvec, p.nmu, tma, &L);
-        cudaError_t ce = L.fn(&p, L.grid, L.block, st);  // warm-up
-        if (ce != cudaSuccess) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return cuda_fail(ce, "tuning launch");
+        plan_launch(ent, nvec, nmu, tma, &L);
+        cudaError_t ce = L.fn(params, L.grid, L.block, st);  // warm-up
+        float ms = 1e30f;
+        for (int trial = 0; trial < 2 && ce == cudaSuccess; ++trial) {
+          ce = cudaEventRecord(e0, st);
+          for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = L.fn(params, L.grid, L.block, st);
+          if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+          if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+          float t = 0.f;
+          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+          if (ce == cudaSuccess && t / 3.f < ms) ms = t / 3.f;
         }
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; ++r) L.fn(&p, L.grid, L.block, st);
-        cudaEventRecord(e1, st);
-        ce = cudaEventSynchronize(e1);
         if (ce != cudaSuccess) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return cuda_fail(ce, "tuning run");
+          rc = cuda_fail(ce, "tuning launch");
+          break;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= 3.f;
         if (ms < best) {
           best = ms;
           bt = th;
           bb = bps;
           bv = L.variant;
         }
+      }
+      if (rc != SU3S_OK) break;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_geometry(ent->kernel[0], p.nvec, p.nmu, bt, bb, bv);
+  if (rc != SU3S_OK) return rc;
+  set_geometry(ent->kernel[0], nvec, nmu, bt, bb, bv);
   if (threads_out) *threads_out = bt;
   if (variant_out) *variant_out = bv;
   if (bps_out) *bps_out = bb;
   if (best_ms) *best_ms = best;
   return ok();
+}
+
+SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream,
+                          int* threads_out, int* bps_out, int* variant_out, float* best_ms) {
+  Canon c;
+  int rc = check_eval(dest, e, &c);
+  if (rc) return rc;
+  if (!valid_math(math)) return fail(SU3S_EINVAL, "bad arithmetic %d", math);
+  const int m = math_for(dest->prec, math);
+  const EvalEntry* ent = find_eval(c.sig, dest->prec, m);
+  if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s", c.sig.c_str());
+  KParams p;
+  build_params(c, dest, ent->vps, &p);
+  return tune_entry(ent, &p, p.nvec, p.nmu, tma_layout_ok(dest), (cudaStream_t)stream,
+                    threads_out, bps_out, variant_out, best_ms);
 }
 
 SU3S_EXPORT int su3s_set_pipeline(int mode) {
@@ -819,8 +847,9 @@ SU3S_EXPORT int su3s_device_error(int* code, void* stream) {
 }
 
 // ---------------------------------------------------------------- adjoint
-SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
-                                  su3s_field* const* gleaves, int nleaves, int math, void* stream) {
+// Checks and kernel parameters of a reverse-mode evaluation.
+static int prepare_adjoint(const su3s_expr* e, const su3s_field* gout, su3s_field* const* gleaves,
+                           int nleaves, int math, GParams* p, const EvalEntry** ent, bool* tma) {
   if (!e || !gout) return fail(SU3S_EINVAL, "null argument");
   Canon c;
   int rc = canonicalize(e, &c);
@@ -842,20 +871,42 @@ SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
   }
   if (!valid_math(math)) return fail(SU3S_EINVAL, "bad arithmetic %d", math);
   const int m = math_for(SU3S_F64, math);
-  const EvalEntry* ent = find_adjoint(c.sig, m);
-  if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled adjoint kernel for %s", c.sig.c_str());
+  *ent = find_adjoint(c.sig, m);
+  if (!*ent) return fail(SU3S_EUNSUPPORTED, "no compiled adjoint kernel for %s", c.sig.c_str());
+  memset(p, 0, sizeof *p);
+  build_params(c, gout, 1, &p->k);
+  p->gout = gout->desc;
+  for (size_t i = 0; i < c.leaves.size(); ++i)
+    if (gleaves && gleaves[i]) p->gleaf[i] = gleaves[i]->desc;
+  *tma = tma_layout_ok(gout);
+  for (size_t i = 0; i < c.leaves.size(); ++i)
+    if (gleaves && gleaves[i]) *tma = *tma && tma_layout_ok(gleaves[i]);
+  return SU3S_OK;
+}
+
+SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
+                                  su3s_field* const* gleaves, int nleaves, int math, void* stream) {
   GParams p;
-  memset(&p, 0, sizeof p);
-  build_params(c, gout, 1, &p.k);
-  p.gout = gout->desc;
-  for (size_t i = 0; i < c.leaves.size(); ++i)
-    if (gleaves && gleaves[i]) p.gleaf[i] = gleaves[i]->desc;
+  const EvalEntry* ent = nullptr;
+  bool tma = false;
+  int rc = prepare_adjoint(e, gout, gleaves, nleaves, math, &p, &ent, &tma);
+  if (rc) return rc;
   Launch L;
-  bool tma = tma_layout_ok(gout);
-  for (size_t i = 0; i < c.leaves.size(); ++i)
-    if (gleaves && gleaves[i]) tma = tma && tma_layout_ok(gleaves[i]);
   plan_launch(ent, p.k.nvec, p.k.nmu, tma, &L);
   cudaError_t ce = L.fn(&p, L.grid, L.block, (cudaStream_t)stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "adjoint kernel launch");
   return ok();
+}
+
+SU3S_EXPORT int su3s_tune_adjoint(const su3s_expr* e, const su3s_field* gout,
+                                  su3s_field* const* gleaves, int nleaves, int math, void* stream,
+                                  int* threads_out, int* bps_out, int* variant_out,
+                                  float* best_ms) {
+  GParams p;
+  const EvalEntry* ent = nullptr;
+  bool tma = false;
+  int rc = prepare_adjoint(e, gout, gleaves, nleaves, math, &p, &ent, &tma);
+  if (rc) return rc;
+  return tune_entry(ent, &p, p.k.nvec, p.k.nmu, tma, (cudaStream_t)stream, threads_out, bps_out,
+                    variant_out, best_ms);
 }

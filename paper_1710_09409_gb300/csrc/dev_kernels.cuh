@@ -833,11 +833,7 @@ struct Sig<Adj<X>> {
 // Registry hooks implemented by the library (api.cu).  A TMA-staged variant
 // (null for reduced-precision storage) is registered beside the plain one,
 // with its tile bytes per warp.
-// Default data movement of a tree (measured on the GB300 at 48^4, FP64
-// storage, pair arithmetic): trees that read a leaf twice or nest products are
-// issue-bound and keep plain loads; trees of at most two leaves stage whole
-// tiles; sums of products of distinct leaves stage leaf by leaf, in forward
-// and reverse mode.
+// Shape predicates of a tree used to pick its default launch.
 template <class T, int I>
 struct AnyRepeat {
   static constexpr bool value = Count<T, I>::value > 1 || AnyRepeat<T, I - 1>::value;
@@ -870,12 +866,31 @@ template <class X, class Y>
 struct IsSumOfProds<Sub<X, Y>> {
   static constexpr bool value = IsProd<X>::value && IsProd<Y>::value;
 };
-template <class Tree, bool GRAD>
-constexpr int default_variant() {
-  if (AnyRepeat<Tree, Tree::nleaf - 1>::value) return 0;
-  if (Tree::nleaf <= 2) return 1;
-  if (IsSumOfProds<Tree>::value) return 2;
-  return 0;
+// Default launch of a tree when the caller set none: data movement variant,
+// threads per block, blocks per SM (0: as many as fit, or one site per thread
+// for plain loads).  The rules restate the fastest candidates of the autotuner
+// (su3s_tune, su3s_tune_adjoint) on the GB300 at 48^4 and 32^4, FP64 storage.
+struct DefaultGeo {
+  int variant, threads, bps;
+};
+template <class Tree, class M, bool GRAD>
+constexpr DefaultGeo default_geometry() {
+  constexpr bool repeat = AnyRepeat<Tree, Tree::nleaf - 1>::value;
+  constexpr bool small = Tree::nleaf <= 2;
+  constexpr bool sum_of_prods = IsSumOfProds<Tree>::value;
+  if constexpr (M::kScaled) {
+    // fixed point: integer latency favours many small blocks with plain loads
+    // for products; sums of products stage whole tiles
+    if (repeat) return DefaultGeo{0, 64, 0};
+    if (small) return GRAD ? DefaultGeo{0, 64, 0} : DefaultGeo{0, 64, 0};
+    if (sum_of_prods) return GRAD ? DefaultGeo{1, 128, 4} : DefaultGeo{1, 256, 2};
+    return DefaultGeo{1, 128, 2};
+  } else {
+    if (repeat) return DefaultGeo{0, 64, 0};
+    if (small) return DefaultGeo{1, 256, 4};
+    if (sum_of_prods) return GRAD ? DefaultGeo{2, 64, 0} : DefaultGeo{0, 64, 0};
+    return DefaultGeo{2, 128, 0};
+  }
 }
 
 // Kernel variants of one tree: 0 plain loads, 1 TMA-staged eagerly (whole
@@ -885,6 +900,8 @@ struct Variants {
   const void* kernel[3];
   int warp_bytes[3];  // shared memory per warp (0 for plain loads)
   int default_variant;
+  int default_threads;  // 0: library default
+  int default_bps;
 };
 void register_eval(const std::string& sig, int prec, int math, const Variants& v, int vps);
 void register_adjoint(const std::string& sig, int math, const Variants& v);
@@ -901,7 +918,10 @@ void reg_eval(int math) {
     v.fn[2] = &launch_eval_lazy<Tree, M, PREC>;
     v.kernel[2] = (const void*)&k_eval_lazy<Tree, M, PREC>;
     v.warp_bytes[2] = LazyLayout<Tree, PREC, false>::STRIDE;
-    v.default_variant = default_variant<Tree, false>();
+    constexpr DefaultGeo g = default_geometry<Tree, M, false>();
+    v.default_variant = g.variant;
+    v.default_threads = g.threads;
+    v.default_bps = g.bps;
   }
   register_eval(Sig<Tree>::str(), PREC, math, v, Vps<PREC>::value);
 }
@@ -917,7 +937,10 @@ void reg_adjoint(int math) {
   v.fn[2] = &launch_adjoint_lazy<Tree, M>;
   v.kernel[2] = (const void*)&k_adjoint_lazy<Tree, M>;
   v.warp_bytes[2] = LazyLayout<Tree, P_F64, true>::STRIDE;
-  v.default_variant = default_variant<Tree, true>();
+  constexpr DefaultGeo g = default_geometry<Tree, M, true>();
+  v.default_variant = g.variant;
+  v.default_threads = g.threads;
+  v.default_bps = g.bps;
   register_adjoint(Sig<Tree>::str(), math, v);
 }
 

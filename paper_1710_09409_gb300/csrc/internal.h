@@ -66,6 +66,8 @@ struct EvalEntry {
   int warp_bytes[kNumVariants];  // shared memory per warp of the staged variants
   int vps;
   int default_variant;           // chosen when no geometry is set
+  int default_threads;           // 0: 128 staged / 256 plain
+  int default_bps;               // blocks per SM, 0: occupancy / full grid
 };
 
 // A resolved launch: which variant, and its geometry.
@@ -81,6 +83,7 @@ void ensure_registered();
 
 // launch geometry (tuned or default) for a kernel over nvec site vectors
 void launch_geometry(const void* kernel, int64_t nvec, int nmu, dim3* grid, dim3* block);
+void plain_geometry(int threads, int bps, int64_t nvec, int nmu, dim3* grid, dim3* block);
 void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int blocks_per_sm,
                   int variant = -1);
 // resolve variant + geometry for an entry; tma_ok: the fields allow 32-site tiles

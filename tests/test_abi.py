@@ -229,6 +229,9 @@ def test_adjoint_validation(L):
     assert L.su3s_eval_adjoint(ab, t.field(su3s.VECTOR), arr, 2, 0, None) == 2
     arr2 = (ctypes.c_void_p * 2)(t.field(su3s.VECTOR), None)
     assert L.su3s_eval_adjoint(ab, g, arr2, 2, 0, None) == 2          # gradient kind
+    assert L.su3s_tune_adjoint(ab, g, arr, 1, 0, None, None, None, None, None) == 1
+    assert L.su3s_tune_adjoint(ab, g, arr2, 2, 0, None, None, None, None, None) == 2
+    assert L.su3s_tune_adjoint(ab, g, arr, 2, 9, None, None, None, None, None) == 1  # arithmetic
 
 
 def test_batch_validation(L):
