@@ -687,7 +687,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the library's autotuner (by default it picks each row's launch "
                          "shape and data movement during setup, outside the timed region)")
-    ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "tma", "tma_leaf"],
+    ap.add_argument("--pipeline", default="auto",
+                    choices=["auto", "plain", "tma", "tma_leaf", "tma_ring"],
                     help="data movement of FP64-storage kernels (default: the library's choice)")
     args = ap.parse_args()
     dims = tuple(int(x) for x in args.dims.split(","))
@@ -736,7 +737,7 @@ def main():
             print(json.dumps(line))
         return 0
     su3s.set_pipeline({"auto": su3s.PIPE_AUTO, "plain": su3s.PIPE_PLAIN, "tma": su3s.PIPE_TMA,
-                       "tma_leaf": su3s.PIPE_TMA_LEAF}[args.pipeline])
+                       "tma_leaf": su3s.PIPE_TMA_LEAF, "tma_ring": su3s.PIPE_TMA_RING}[args.pipeline])
     stream = torch.cuda.Stream()
     with_host = not args.no_e2e
     rows, keep = build_rows(su3s, synth, torch, with_host, dims, want)

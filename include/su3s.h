@@ -267,7 +267,11 @@ int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int th
  *    1  TMA-staged tiles: each warp stages its next 32-site tile of every leaf
  *       with bulk copies into shared memory while it computes the current one;
  *    2  TMA-staged per leaf: each leaf has its own buffer and barrier, is read
- *       when first needed and refilled after its last use.
+ *       when first needed and refilled after its last use;
+ *    3  TMA-staged through a ring of three buffers per warp, for trees that
+ *       read every object once per tile (others use their default): reading
+ *       the object at position j of the tile's read order hands its buffer to
+ *       position j + 3, of this tile or of the warp's next one.
  * All modes give bitwise identical results.  Staging needs 32 sites of a
  * component to be contiguous (SOA, or AOSOA with block >= 32); otherwise plain
  * loads are used.  EINVAL for other values. */
@@ -297,12 +301,13 @@ int su3s_batch_create(su3s_batch** out);
 /* Queue dest = e.  The batch keeps references to the expression; fields must
  * outlive the batch.  Items must use FP64 storage. */
 int su3s_batch_add(su3s_batch* b, su3s_field* dest, const su3s_expr* e);
-/* Freeze the batch: build the tile list (tile_sites sites per tile; 0 = the
- * library's choice) and item table in library-owned device memory, choose
- * the persistent grid (threads per block; 0 = default) and capture the
- * launch into a CUDA graph on `stream`.  Items whose tree the persistent
- * kernel does not cover are captured as separate launches in the same graph.
- * math as for su3s_eval_math. */
+/* Freeze the batch: build the tile list (tile_sites sites per tile; 0 = 2 x
+ * threads) and item table in library-owned device memory, choose the
+ * persistent grids (threads per block, a multiple of 32 up to 256; 0 = 256)
+ * and capture the launches into a CUDA graph on `stream`: one persistent
+ * kernel per tree present in the batch, compiled for that tree.  Items whose
+ * tree no persistent kernel covers are captured as separate launches in the
+ * same graph.  math as for su3s_eval_math. */
 int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_sites, void* stream);
 /* Replay the graph on `stream`. */
 int su3s_batch_launch(su3s_batch* b, void* stream);

@@ -136,12 +136,14 @@ def set_default_math(math):
     _check(load().su3s_set_default_math(math))
 
 
-PIPE_AUTO, PIPE_PLAIN, PIPE_TMA, PIPE_TMA_LEAF = -1, 0, 1, 2
+PIPE_AUTO, PIPE_PLAIN, PIPE_TMA, PIPE_TMA_LEAF, PIPE_TMA_RING = -1, 0, 1, 2, 3
 
 
 def set_pipeline(mode):
     """-1 the library's choice, 0 plain loads, 1 TMA-staged tiles, 2 TMA-staged
-    per leaf (FP64 storage; layouts that keep 32 sites contiguous)."""
+    per leaf, 3 TMA-staged through a ring of buffers (FP64 storage; layouts
+    that keep 32 sites contiguous; trees without a ring kernel use their
+    default)."""
     _check(load().su3s_set_pipeline(mode))
 
 

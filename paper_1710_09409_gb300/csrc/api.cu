@@ -189,7 +189,7 @@ int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* 
   if (!can_stage) variant = 0;
   if (variant > 0) {
     int threads = g.threads > 0 ? g.threads : 128;
-    if (variant == 2 && threads > 128) threads = 128;  // per-leaf kernels: at most 4 warps
+    if (variant >= 2 && threads > 128) threads = 128;  // per-leaf / ring kernels: at most 4 warps
     const int occ = staged_occupancy(e->kernel[variant], threads, e->warp_bytes[variant]);
     const int per_sm = g.bps > 0 && g.bps < occ ? g.bps : occ;
     const int64_t ntiles = nvec / 32, wpb = threads / 32;
@@ -771,7 +771,7 @@ static int tune_entry(const EvalEntry* ent, const void* params, int64_t nvec, in
   for (int var = 0; var < (tma ? kNumVariants : 1) && rc == SU3S_OK; ++var) {
     if (!ent->fn[var]) continue;
     for (int th : th_c) {
-      if (var == 2 && th > 128) continue;  // per-leaf kernels take at most 4 warps
+      if (var >= 2 && th > 128) continue;  // per-leaf / ring kernels take at most 4 warps
       for (int bps : bps_c) {
         set_geometry(ent->kernel[0], nvec, nmu, th, bps, var);
         Launch L;
@@ -828,7 +828,7 @@ SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* 
 }
 
 SU3S_EXPORT int su3s_set_pipeline(int mode) {
-  if (mode < -1 || mode > 2) return fail(SU3S_EINVAL, "pipeline mode must be -1, 0, 1 or 2");
+  if (mode < -1 || mode > 3) return fail(SU3S_EINVAL, "pipeline mode must be -1, 0, 1, 2 or 3");
   g_pipeline_pref = mode;
   return ok();
 }

@@ -1,10 +1,11 @@
 // Batched evaluation: many (destination, tree) items over lattices of uneven
-// volumes run in one persistent kernel.  The host cuts every item into tiles
-// of site vectors; a fixed grid of blocks (sized from occupancy) walks the
-// tile list round-robin, and each tile dispatches on its item's tree (uniform
-// within the block).  The launch, plus separate launches for items whose tree
-// the persistent kernel does not cover, is captured once into a CUDA graph
-// and replayed with a single cudaGraphLaunch.
+// volumes run in persistent kernels, one per tree present in the batch (each
+// compiled for its tree alone, so its register use is that tree's).  The host
+// cuts every item into tiles of site vectors and groups the tiles by tree; for
+// each group a fixed grid of blocks (sized from occupancy) walks its tile list
+// round-robin.  These launches, plus separate launches for items whose tree no
+// persistent kernel covers, are captured once into a CUDA graph and replayed
+// with a single cudaGraphLaunch.
 #include <string.h>
 
 #include <string>
@@ -42,26 +43,46 @@ static const char* const kBatchTrees[] = {
 };
 constexpr int kNumBatchTrees = 8;
 
-template <class M>
-__global__ void __launch_bounds__(256) k_batch(const BItem* __restrict__ items,
-                                               const BTile* __restrict__ tiles, int64_t ntiles) {
+// At most 128 registers: two 256-thread blocks (16 warps) per SM.  The
+// item's parameters are copied to shared memory once per tile, so the site
+// loop reads them with broadcast shared-memory loads.
+template <class M, class Tree>
+__global__ void __launch_bounds__(256, 2) k_batch(const BItem* __restrict__ items,
+                                                  const BTile* __restrict__ tiles, int64_t ntiles) {
+  __shared__ KParams sk;
+  constexpr int kWords = (int)(sizeof(KParams) / 4);
+  static_assert(sizeof(KParams) % 4 == 0, "KParams is copied as 32-bit words");
   for (int64_t i = blockIdx.x; i < ntiles; i += gridDim.x) {
     const BTile T = tiles[i];
-    const BItem& it = items[T.item];
-    const int tree = it.tree;
-    for (int64_t t = T.t0 + threadIdx.x; t < T.t1; t += blockDim.x) {
-      switch (tree) {
-        case 0: eval_sites<cat::MM, M, P_F64>(it.k, t, T.mu); break;
-        case 1: eval_sites<cat::E1, M, P_F64>(it.k, t, T.mu); break;
-        case 2: eval_sites<cat::MV, M, P_F64>(it.k, t, T.mu); break;
-        case 3: eval_sites<cat::E2, M, P_F64>(it.k, t, T.mu); break;
-        case 4: eval_sites<cat::E3, M, P_F64>(it.k, t, T.mu); break;
-        case 5: eval_sites<cat::MMM, M, P_F64>(it.k, t, T.mu); break;
-        case 6: eval_sites<cat::E1Lin, M, P_F64>(it.k, t, T.mu); break;
-        default: eval_sites<cat::AdjMM, M, P_F64>(it.k, t, T.mu); break;
-      }
-    }
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&items[T.item].k);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sk);
+    for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    for (int64_t t = T.t0 + threadIdx.x; t < T.t1; t += blockDim.x)
+      eval_sites<Tree, M, P_F64>(sk, t, T.mu);
+    __syncthreads();
   }
+}
+
+// Persistent kernel of batch tree `tree` in arithmetic M.
+template <class M>
+static const void* batch_kernel(int tree) {
+  switch (tree) {
+    case 0: return (const void*)&k_batch<M, cat::MM>;
+    case 1: return (const void*)&k_batch<M, cat::E1>;
+    case 2: return (const void*)&k_batch<M, cat::MV>;
+    case 3: return (const void*)&k_batch<M, cat::E2>;
+    case 4: return (const void*)&k_batch<M, cat::E3>;
+    case 5: return (const void*)&k_batch<M, cat::MMM>;
+    case 6: return (const void*)&k_batch<M, cat::E1Lin>;
+    default: return (const void*)&k_batch<M, cat::AdjMM>;
+  }
+}
+
+static const void* batch_kernel(int math, int tree) {
+  return math == MATH_F64  ? batch_kernel<MathF64>(tree)
+         : math == MATH_FX ? batch_kernel<MathFX>(tree)
+                           : batch_kernel<MathDF>(tree);
 }
 
 }  // namespace su3s
@@ -124,7 +145,7 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   if (threads == 0) threads = 256;
   if (threads < 32 || threads > 256 || threads % 32)
     return fail(SU3S_EINVAL, "threads per block must be a multiple of 32 in 32..256");
-  if (tile_sites == 0) tile_sites = 4 * threads;
+  if (tile_sites == 0) tile_sites = 2 * threads;
   if (tile_sites < threads) return fail(SU3S_EINVAL, "tile smaller than a block");
   if (!valid_math(math))
     return fail(SU3S_EINVAL, "bad arithmetic %d", math);
@@ -132,7 +153,7 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   (void)stream;
 
   std::vector<BItem> hitems;
-  std::vector<BTile> htiles;
+  std::vector<BTile> by_tree[kNumBatchTrees];
   std::vector<size_t> others;  // item indices launched separately
   int64_t nsites = 0;
   for (size_t i = 0; i < b->items.size(); ++i) {
@@ -155,8 +176,16 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     for (int mu = 0; mu < it.k.nmu; ++mu)
       for (int64_t t0 = 0; t0 < it.k.nvec; t0 += tile_sites) {
         int64_t t1 = t0 + tile_sites < it.k.nvec ? t0 + tile_sites : it.k.nvec;
-        htiles.push_back(BTile{idx, mu, t0, t1});
+        by_tree[tree].push_back(BTile{idx, mu, t0, t1});
       }
+  }
+  // tiles grouped by tree: group t is htiles[first[t], first[t] + count[t])
+  std::vector<BTile> htiles;
+  int64_t first[kNumBatchTrees], count[kNumBatchTrees];
+  for (int t = 0; t < kNumBatchTrees; ++t) {
+    first[t] = (int64_t)htiles.size();
+    count[t] = (int64_t)by_tree[t].size();
+    htiles.insert(htiles.end(), by_tree[t].begin(), by_tree[t].end());
   }
   b->nsites = nsites;
   b->ntiles = (int64_t)htiles.size();
@@ -178,16 +207,17 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     }
   }
 
-  // persistent grid from occupancy
-  const void* kern = m == MATH_F64  ? (const void*)&k_batch<MathF64>
-                     : m == MATH_FX ? (const void*)&k_batch<MathFX>
-                                    : (const void*)&k_batch<MathDF>;
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)per_sm * sm_count();
-  if (grid > b->ntiles) grid = b->ntiles;
-  if (grid < 1) grid = 1;
+  // persistent grid of each group from its kernel's occupancy
+  int64_t grid[kNumBatchTrees];
+  for (int t = 0; t < kNumBatchTrees; ++t) {
+    int per_sm = 1;
+    if (count[t] > 0)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(m, t), threads, 0);
+    if (per_sm < 1) per_sm = 1;
+    grid[t] = (int64_t)per_sm * sm_count();
+    if (grid[t] > count[t]) grid[t] = count[t];
+    if (grid[t] < 1) grid[t] = 1;
+  }
 
   cudaStream_t cap;
   ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
@@ -198,11 +228,14 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int rc = SU3S_OK;
   if (ce == cudaSuccess) {
-    if (b->ntiles > 0) {
-      if (m == MATH_F64) k_batch<MathF64><<<(unsigned)grid, threads, 0, cap>>>(b->d_items, b->d_tiles, b->ntiles);
-      else if (m == MATH_FX) k_batch<MathFX><<<(unsigned)grid, threads, 0, cap>>>(b->d_items, b->d_tiles, b->ntiles);
-      else k_batch<MathDF><<<(unsigned)grid, threads, 0, cap>>>(b->d_items, b->d_tiles, b->ntiles);
-      ce = cudaGetLastError();
+    for (int t = 0; t < kNumBatchTrees && !rc; ++t) {
+      if (count[t] == 0) continue;
+      const BItem* items = b->d_items;
+      const BTile* tiles = b->d_tiles + first[t];
+      int64_t n = count[t];
+      void* args[] = {(void*)&items, (void*)&tiles, (void*)&n};
+      ce = cudaLaunchKernel(batch_kernel(m, t), dim3((unsigned)grid[t]), dim3((unsigned)threads),
+                            args, 0, cap);
       if (ce != cudaSuccess) rc = cuda_fail(ce, "persistent kernel capture");
     }
     for (size_t i : others) {

@@ -715,6 +715,326 @@ __global__ void __launch_bounds__(128, 3) k_adjoint_lazy(const __grid_constant__
   adj_lazy_range<Tree, M>(p, warp_range(p.k.nvec >> 5), smem);
 }
 
+// ------------------------------------------- ring-staged variant
+// For trees that read every object (leaf, and dL/dZ in reverse mode) exactly
+// once per tile, in an order fixed at compile time: K <= (objects) rotating
+// buffers per warp, position j of a tile's read order using buffer j % K.
+// Reading position j frees its buffer for that buffer's next position: j + K
+// of this tile if there is one, else position j % K of the warp's next tile.
+// Each copy then has about K positions' worth of compute to land, while a
+// warp holds K object buffers instead of one per object.
+
+// Read order of leaf slots, as lists built at compile time.
+struct SlotSeq {
+  int s[16];
+  int n;
+};
+__host__ __device__ constexpr SlotSeq seq_empty() { return SlotSeq{{0}, 0}; }
+__host__ __device__ constexpr SlotSeq seq_one(int slot) {
+  SlotSeq r{{0}, 1};
+  r.s[0] = slot;
+  return r;
+}
+__host__ __device__ constexpr SlotSeq seq_cat(SlotSeq a, SlotSeq b) {
+  for (int i = 0; i < b.n && a.n < 16; ++i) a.s[a.n++] = b.s[i];
+  return a;
+}
+__host__ __device__ constexpr SlotSeq seq_cat(SlotSeq a, SlotSeq b, SlotSeq c, SlotSeq d) {
+  return seq_cat(seq_cat(a, b), seq_cat(c, d));
+}
+
+// Forward evaluation reads operands left to right (value, acc_into).
+template <class T>
+struct FwdSeq {
+  __host__ __device__ static constexpr SlotSeq get() { return seq_one(T::slot); }
+};
+template <class X, class Y>
+struct FwdSeq<Mul<X, Y>> {
+  __host__ __device__ static constexpr SlotSeq get() {
+    return seq_cat(FwdSeq<typename Operand<X>::base>::get(), FwdSeq<typename Operand<Y>::base>::get());
+  }
+};
+template <class X, class Y>
+struct FwdSeq<Add<X, Y>> {
+  __host__ __device__ static constexpr SlotSeq get() { return seq_cat(FwdSeq<X>::get(), FwdSeq<Y>::get()); }
+};
+template <class X, class Y>
+struct FwdSeq<Sub<X, Y>> {
+  __host__ __device__ static constexpr SlotSeq get() { return seq_cat(FwdSeq<X>::get(), FwdSeq<Y>::get()); }
+};
+template <int K, class X>
+struct FwdSeq<Scale<K, X>> {
+  __host__ __device__ static constexpr SlotSeq get() { return FwdSeq<X>::get(); }
+};
+template <class X>
+struct FwdSeq<Adj<X>> {
+  __host__ __device__ static constexpr SlotSeq get() { return FwdSeq<X>::get(); }
+};
+
+// Reverse mode (Rev::run): a product reads Y's value, back-propagates into X,
+// reads X's value, back-propagates into Y; leaves read nothing.
+template <class T>
+struct RevSeq {
+  __host__ __device__ static constexpr SlotSeq get() { return seq_empty(); }
+};
+template <class X, class Y>
+struct RevSeq<Mul<X, Y>> {
+  using BX = typename Operand<X>::base;
+  using BY = typename Operand<Y>::base;
+  __host__ __device__ static constexpr SlotSeq get() {
+    return seq_cat(FwdSeq<BY>::get(), RevSeq<BX>::get(), FwdSeq<BX>::get(), RevSeq<BY>::get());
+  }
+};
+template <class X, class Y>
+struct RevSeq<Add<X, Y>> {
+  __host__ __device__ static constexpr SlotSeq get() { return seq_cat(RevSeq<X>::get(), RevSeq<Y>::get()); }
+};
+template <class X, class Y>
+struct RevSeq<Sub<X, Y>> {
+  __host__ __device__ static constexpr SlotSeq get() { return seq_cat(RevSeq<X>::get(), RevSeq<Y>::get()); }
+};
+template <int K, class X>
+struct RevSeq<Scale<K, X>> {
+  __host__ __device__ static constexpr SlotSeq get() { return RevSeq<X>::get(); }
+};
+template <class X>
+struct RevSeq<Adj<X>> {
+  __host__ __device__ static constexpr SlotSeq get() { return RevSeq<X>::get(); }
+};
+
+// Objects of a tile in read order; dL/dZ is slot nleaf and comes first.
+template <class Tree, bool GRAD>
+struct ReadSeq {
+  __host__ __device__ static constexpr SlotSeq get() {
+    if constexpr (GRAD) return seq_cat(seq_one(Tree::nleaf), RevSeq<Tree>::get());
+    else return FwdSeq<Tree>::get();
+  }
+};
+
+template <class Tree, bool GRAD>
+__host__ __device__ constexpr int seq_pos(int slot) {
+  constexpr SlotSeq q = ReadSeq<Tree, GRAD>::get();
+  for (int i = 0; i < q.n; ++i)
+    if (q.s[i] == slot) return i;
+  return -1;
+}
+
+// Whether every object is read exactly once (the ring's requirement).
+template <class Tree, bool GRAD>
+__host__ __device__ constexpr bool ring_ok() {
+  constexpr SlotSeq q = ReadSeq<Tree, GRAD>::get();
+  constexpr int nobj = Tree::nleaf + (GRAD ? 1 : 0);
+  if (q.n != nobj || nobj < 3) return false;
+  for (int slot = 0; slot < nobj; ++slot) {
+    int c = 0;
+    for (int i = 0; i < q.n; ++i) c += q.s[i] == slot;
+    if (c != 1) return false;
+  }
+  return true;
+}
+
+// Position that buffer j % K serves after position j of a tile (n objects):
+// j + K of the same tile, else j % K of the next tile.
+__host__ __device__ constexpr int ring_next(int j, int n, int K) { return j + K < n ? j + K : j % K; }
+
+// The schedule, checked at compile time over three tiles: every buffer
+// alternates strictly between one copy in flight and one read.
+template <class Tree, bool GRAD, int K>
+__host__ __device__ constexpr bool ring_schedule_ok() {
+  constexpr int n = Tree::nleaf + (GRAD ? 1 : 0);
+  int busy[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // copies in flight per buffer
+  for (int j = 0; j < K && j < n; ++j) busy[j % K] += 1;
+  for (int t = 0; t < 3; ++t)
+    for (int j = 0; j < n; ++j) {
+      const int b = j % K;
+      if (busy[b] != 1) return false;  // the read must find exactly its copy
+      busy[b] = 0;
+      const int nj = ring_next(j, n, K);
+      if (nj % K != b) return false;
+      busy[b] += 1;
+    }
+  return true;
+}
+
+template <class Tree, int PREC, bool GRAD>
+struct RingLayout {
+  static constexpr int NOBJ = Tree::nleaf + (GRAD ? 1 : 0);
+  static constexpr int K = NOBJ > 3 ? 3 : NOBJ;                   // buffers per warp
+  static constexpr int BUF = StageBytes<KM, PREC>::value;         // largest object
+  static constexpr int DATA = K * BUF;
+  static constexpr int STRIDE = (DATA + 8 * K + 15) / 16 * 16;
+};
+
+template <class Tree, class M, int PREC, bool GRAD>
+struct RingCtx {
+  using L = RingLayout<Tree, PREC, GRAD>;
+  static constexpr int NL = Tree::nleaf;
+  static constexpr int NS = Tree::nsc;
+  static constexpr SlotSeq kSeq = ReadSeq<Tree, GRAD>::get();
+  static_assert(ring_schedule_ok<Tree, GRAD, L::K>(), "ring schedule reuses a busy buffer");
+  unsigned char* buf;
+  uint64_t* bars;
+  const KParams* p;
+  const FieldDesc* gout;
+  int64_t cur_s0, next_s0;
+  int mu, lane;
+  mutable uint32_t ph;  // barrier parity of each buffer
+  bool has_next;
+  mutable bool dead;
+  typename M::R sc[NS > 0 ? NS : 1];
+
+  template <int I>
+  __device__ __forceinline__ void issue(int64_t s0, int b) const {
+    constexpr int K = I < NL ? LeafKind<Tree, (I < NL ? I : 0)>::value : Tree::kind;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[b], StageBytes<K, PREC>::value);
+    __syncwarp();
+    const FieldDesc& f = I < NL ? p->leaf[I < NL ? I : 0] : *gout;
+    issue_if_mine<K, PREC, 0>(lane, f, s0, mu, buf + b * L::BUF, &bars[b]);
+  }
+
+  // issue the object at position j of the tile whose first site is s0
+  template <int J>
+  __device__ __forceinline__ void issue_pos(int64_t s0) const {
+    issue<kSeq.s[J]>(s0, J % L::K);
+  }
+
+  template <int I, int W>
+  __device__ __forceinline__ void leaf_value(typename M::R* out) const {
+    constexpr int j = seq_pos<Tree, GRAD>(I);
+    static_assert(j >= 0, "object outside the read order");
+    constexpr int b = j % L::K;
+    constexpr int K = I < NL ? LeafKind<Tree, (I < NL ? I : 0)>::value : Tree::kind;
+    if (!dead) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[b], (ph >> b) & 1u));
+      if (!ok) {
+        if (lane == 0 && p->err) atomicExch(p->err, kErrTmaTimeout);
+        dead = true;
+      }
+    }
+    ph ^= 1u << b;
+    Ctx<M, 1, 0> tmp;
+    read_obj<K, PREC, M>(buf + b * L::BUF, lane, tmp, 0);
+#pragma unroll
+    for (int r = 0; r < W; ++r) out[r] = tmp.leaf[0][r];
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (dead) return;
+    // hand the buffer to its next position (this tile, else the next one)
+    constexpr int nj = ring_next(j, L::NOBJ, L::K);
+    if constexpr (nj > j) issue_pos<nj>(cur_s0);
+    else if (has_next) issue_pos<nj>(next_s0);
+  }
+
+  template <int J>
+  __device__ __forceinline__ void issue_first(int64_t s0) const {
+    if constexpr (J < L::K) {
+      issue_pos<J>(s0);
+      issue_first<J + 1>(s0);
+    }
+  }
+
+  // after a time-out: let copies in flight land (bounded), once per buffer
+  __device__ __forceinline__ void drain() const {
+#pragma unroll
+    for (int b = 0; b < L::K; ++b) mbar_wait_bounded(&bars[b], (ph >> b) & 1u);
+  }
+};
+
+template <class Tree, class M, int PREC, bool GRAD>
+__device__ __forceinline__ void ring_setup(RingCtx<Tree, M, PREC, GRAD>& c, unsigned char* smem,
+                                           const KParams& p, const FieldDesc* gout) {
+  using L = RingLayout<Tree, PREC, GRAD>;
+  const int warp = threadIdx.x >> 5;
+  c.lane = threadIdx.x & 31;
+  c.buf = smem + warp * L::STRIDE;
+  c.bars = reinterpret_cast<uint64_t*>(c.buf + L::DATA);
+  c.p = &p;
+  c.gout = gout;
+  c.mu = blockIdx.y;
+  c.ph = 0;
+  c.dead = false;
+  if (c.lane == 0) {
+#pragma unroll
+    for (int i = 0; i < L::K; ++i) mbar_init(&c.bars[i], 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < (Tree::nsc > 0 ? Tree::nsc : 1); ++k)
+    c.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
+}
+
+template <class Tree, class M, int PREC>
+__device__ __forceinline__ void ring_range(const KParams& p, Range rg, unsigned char* smem) {
+  constexpr int W = Width<Tree::kind>::value;
+  RingCtx<Tree, M, PREC, false> c;
+  ring_setup(c, smem, p, nullptr);
+  const int64_t ntiles = rg.end;
+  int64_t t = rg.first;
+  if (t < ntiles) c.template issue_first<0>(t << 5);
+  while (t < ntiles) {
+    const int64_t tn = t + rg.stride;
+    c.cur_s0 = t << 5;
+    c.has_next = tn < ntiles;
+    c.next_s0 = tn << 5;
+    typename M::A acc[1][W];
+    if constexpr (Tree::accumulates) {
+      acc_into<Tree, M, true, 1>(c, acc[0]);
+    } else {
+      typename M::R val[W];
+      value<Tree, M>(c, val);
+#pragma unroll
+      for (int r = 0; r < W; ++r) acc[0][r] = M::to_acc(val[r]);
+    }
+    if (c.dead) break;
+    store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
+    t = tn;
+  }
+  if (c.dead) c.drain();
+}
+
+template <class Tree, class M, int PREC>
+__global__ void __launch_bounds__(128, 4) k_eval_ring(const __grid_constant__ KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  ring_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);
+}
+
+template <class Tree, class M>
+__device__ __forceinline__ void adj_ring_range(const GParams& p, Range rg, unsigned char* smem) {
+  constexpr int NL = Tree::nleaf;
+  constexpr int W = Width<Tree::kind>::value;
+  RingCtx<Tree, M, P_F64, true> c;
+  ring_setup(c, smem, p.k, &p.gout);
+  const int64_t ntiles = rg.end;
+  int64_t t = rg.first;
+  if (t < ntiles) c.template issue_first<0>(t << 5);
+  while (t < ntiles) {
+    const int64_t tn = t + rg.stride;
+    c.cur_s0 = t << 5;
+    c.has_next = tn < ntiles;
+    c.next_s0 = tn << 5;
+    typename M::R G[W];
+    c.template leaf_value<NL, W>(G);   // dL/dZ
+    GradAcc<M, NL> ga;
+#pragma unroll
+    for (int i = 0; i < NL; ++i)
+#pragma unroll
+      for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
+    GradSink<Tree, M> sink{&p, (t << 5) + c.lane, c.mu};
+    Rev<Tree>::template run<Tree, M>(c, G, ga, sink);
+    store_repeated<Tree, 0, M>(ga, sink);
+    if (c.dead) break;
+    t = tn;
+  }
+  if (c.dead) c.drain();
+}
+
+template <class Tree, class M>
+__global__ void __launch_bounds__(128, 3) k_adjoint_ring(const __grid_constant__ GParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  adj_ring_range<Tree, M>(p, warp_range(p.k.nvec >> 5), smem);
+}
+
 // ------------------------------------------------------------ launchers
 using LaunchFn = cudaError_t (*)(const void* params, dim3 grid, dim3 block, cudaStream_t st);
 
@@ -789,6 +1109,34 @@ cudaError_t launch_adjoint_lazy(const void* params, dim3 grid, dim3 block, cudaS
     attr = true;
   }
   k_adjoint_lazy<Tree, M><<<grid, block, (block.x / 32) * S, st>>>(*static_cast<const GParams*>(params));
+  return cudaGetLastError();
+}
+
+template <class Tree, class M, int PREC>
+cudaError_t launch_eval_ring(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int S = RingLayout<Tree, PREC, false>::STRIDE;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_eval_ring<Tree, M, PREC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * S);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_eval_ring<Tree, M, PREC><<<grid, block, (block.x / 32) * S, st>>>(*static_cast<const KParams*>(params));
+  return cudaGetLastError();
+}
+
+template <class Tree, class M>
+cudaError_t launch_adjoint_ring(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int S = RingLayout<Tree, P_F64, true>::STRIDE;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_ring<Tree, M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * S);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_adjoint_ring<Tree, M><<<grid, block, (block.x / 32) * S, st>>>(*static_cast<const GParams*>(params));
   return cudaGetLastError();
 }
 
@@ -894,11 +1242,12 @@ constexpr DefaultGeo default_geometry() {
 }
 
 // Kernel variants of one tree: 0 plain loads, 1 TMA-staged eagerly (whole
-// tile), 2 TMA-staged lazily (per leaf).  1 and 2 exist for FP64 storage.
+// tile), 2 TMA-staged lazily (per leaf), 3 TMA-staged through a ring of
+// buffers (trees that read each object once).  1-3 exist for FP64 storage.
 struct Variants {
-  LaunchFn fn[3];
-  const void* kernel[3];
-  int warp_bytes[3];  // shared memory per warp (0 for plain loads)
+  LaunchFn fn[4];
+  const void* kernel[4];
+  int warp_bytes[4];  // shared memory per warp (0 for plain loads)
   int default_variant;
   int default_threads;  // 0: library default
   int default_bps;
@@ -918,6 +1267,11 @@ void reg_eval(int math) {
     v.fn[2] = &launch_eval_lazy<Tree, M, PREC>;
     v.kernel[2] = (const void*)&k_eval_lazy<Tree, M, PREC>;
     v.warp_bytes[2] = LazyLayout<Tree, PREC, false>::STRIDE;
+    if constexpr (ring_ok<Tree, false>()) {
+      v.fn[3] = &launch_eval_ring<Tree, M, PREC>;
+      v.kernel[3] = (const void*)&k_eval_ring<Tree, M, PREC>;
+      v.warp_bytes[3] = RingLayout<Tree, PREC, false>::STRIDE;
+    }
     constexpr DefaultGeo g = default_geometry<Tree, M, false>();
     v.default_variant = g.variant;
     v.default_threads = g.threads;
@@ -937,6 +1291,11 @@ void reg_adjoint(int math) {
   v.fn[2] = &launch_adjoint_lazy<Tree, M>;
   v.kernel[2] = (const void*)&k_adjoint_lazy<Tree, M>;
   v.warp_bytes[2] = LazyLayout<Tree, P_F64, true>::STRIDE;
+  if constexpr (ring_ok<Tree, true>()) {
+    v.fn[3] = &launch_adjoint_ring<Tree, M>;
+    v.kernel[3] = (const void*)&k_adjoint_ring<Tree, M>;
+    v.warp_bytes[3] = RingLayout<Tree, P_F64, true>::STRIDE;
+  }
   constexpr DefaultGeo g = default_geometry<Tree, M, true>();
   v.default_variant = g.variant;
   v.default_threads = g.threads;

@@ -59,7 +59,7 @@ int sm_count();
 
 // kernel registry
 // Variants: 0 plain loads, 1 TMA-staged whole tile, 2 TMA-staged per leaf.
-constexpr int kNumVariants = 3;
+constexpr int kNumVariants = 4;
 struct EvalEntry {
   cudaError_t (*fn[kNumVariants])(const void*, dim3, dim3, cudaStream_t);
   const void* kernel[kNumVariants];

@@ -256,3 +256,11 @@ def test_package_never_reaches_the_oracle():
             src = open(os.path.join(pkg, fn)).read()
             for mod in ("oracle", "synth"):
                 assert "import %s" % mod not in src and "from %s" % mod not in src, fn
+
+
+def test_pipeline_modes(L):
+    for mode in (-1, 0, 1, 2, 3):
+        assert L.su3s_set_pipeline(mode) == 0
+    assert L.su3s_set_pipeline(4) == 1
+    assert L.su3s_set_pipeline(-2) == 1
+    assert L.su3s_set_pipeline(-1) == 0

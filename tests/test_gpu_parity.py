@@ -487,7 +487,9 @@ def test_batch_matches_separate_evaluations(su3s, math):
 @pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2], LAYOUTS[3]], ids=layout_id)
 def test_tma_staging_is_bitwise_identical(su3s, lay, math):
     """The TMA-staged kernels (bulk copies into shared memory, one 32-site tile
-    per warp) and the plain-load kernels run the same arithmetic per site."""
+    per warp: whole tile, per leaf, or through a ring of buffers) and the
+    plain-load kernels run the same arithmetic per site."""
+    PIPES = (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF, su3s.PIPE_TMA_RING)
     dims = (8, 8, 8, 9)
     lat = su3s.Lattice(dims)
     f = lattice_fields(dims, SEED, nmu=4, names=("a", "b", "c", "d", "w"))
@@ -497,23 +499,24 @@ def test_tma_staging_is_bitwise_identical(su3s, lay, math):
     try:
         for e in exprs:
             outs = []
-            for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF):
+            for mode in PIPES:
                 su3s.set_pipeline(mode)
                 z = a.like()
                 su3s.evaluate(z, e, math)
                 outs.append(z.download())
-            assert np.array_equal(outs[0], outs[1])
-            assert np.array_equal(outs[0], outs[2])
+            for o in outs[1:]:
+                assert np.array_equal(outs[0], o)
         grads = []
-        for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF):
+        for mode in PIPES:
             su3s.set_pipeline(mode)
             g = [a.like() for _ in range(4)]
             su3s.eval_adjoint(a * b + c * d, F["w"], g, math)
             g2 = [a.like() for _ in range(4)]
             su3s.eval_adjoint(a * b * c + 0.5 * d, F["w"], g2, math)
             grads.append([x.download() for x in g + g2])
-        for x, y, w in zip(*grads):
-            assert np.array_equal(x, y) and np.array_equal(x, w)
+        for xs in zip(*grads):
+            for y in xs[1:]:
+                assert np.array_equal(xs[0], y)
     finally:
         su3s.set_pipeline(su3s.PIPE_AUTO)
     assert su3s.device_error() == 0
@@ -521,6 +524,40 @@ def test_tma_staging_is_bitwise_identical(su3s, lay, math):
     z = a.like()
     su3s.evaluate(z, a * b + c * d, math)
     assert np.abs(z.download() - ref).max() < 2 * TOL
+
+
+def test_ring_staging_over_many_tiles_per_warp(su3s):
+    """The ring-staged kernels prefetch into the warp's next tile; with many
+    tiles per warp (a small forced grid, and a 24^4 lattice for the reverse
+    mode) they stay bitwise equal to plain loads."""
+    dims = (24, 24, 24, 24)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED + 11, names=("a", "b", "c", "d", "w"))
+    F = {n: upload(su3s, lat, f[n]) for n in "abcdw"}
+    a, b, c, d = (F[n] for n in "abcd")
+    try:
+        for math in MATHS:
+            for e in (a * b + c * d, a * b * c + 0.5 * d):
+                outs = []
+                for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA_RING):
+                    su3s.set_pipeline(mode)
+                    z = a.like()
+                    su3s.set_launch(z, e, 32, 1, math)   # 152 one-warp blocks: ~68 tiles each
+                    su3s.evaluate(z, e, math)
+                    outs.append(z.download())
+                assert np.array_equal(outs[0], outs[1])
+            for e, n in ((a * b + c * d, 4), (a * b, 2)):
+                gs = []
+                for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA_RING):
+                    su3s.set_pipeline(mode)
+                    g = [a.like() for _ in range(n)]
+                    su3s.eval_adjoint(e, F["w"], g, math)
+                    gs.append([x.download() for x in g])
+                for x, y in zip(*gs):
+                    assert np.array_equal(x, y)
+    finally:
+        su3s.set_pipeline(su3s.PIPE_AUTO)
+    assert su3s.device_error() == 0
 
 
 # ---------------------------------------------------------- tuning
