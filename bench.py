@@ -58,17 +58,7 @@ MATH_DESC = {"fx": "shared-exponent fixed-point (fx)", "df32": "pair-of-FP32 (df
 # stand; scaled to the benchmark's volume in proportion to the sites (the
 # algorithmic bytes).  (row, kernel whose counters these are, bytes, algorithmic
 # bytes of that launch).  A row missing here reports traffic null.
-TRAFFIC_32 = {
-    "A2 z=a*b": ("k_eval_tma<Mul<LM<0>,LM<1>>,MathDF,0>", (302.0 + 112.3) * 1e6, 432 * 1048576),
-    "A4 z_mu=a_mu*b_mu": ("k_eval_tma<Mul<LM<0>,LM<1>>,MathDF,0>", (1208.0 + 570.5) * 1e6,
-                          4 * 432 * 1048576),
-    "A5 z=a*b+c*d": ("k_eval_lazy<E1,MathDF,0>", (604.8 + 125.4) * 1e6, 720 * 1048576),
-    "A5 z=a*b*c+0.5*d": ("k_eval<E2,MathDF,0>", (604.1 + 123.3) * 1e6, 720 * 1048576),
-    "A5 z=adj(a)*b-b*adj(a)": ("k_eval<E3,MathDF,0>", (302.1 + 110.4) * 1e6, 432 * 1048576),
-    "A9 adjoint of z=a*b": ("k_adjoint_tma<MM,MathDF>", (453.1 + 253.5) * 1e6, 720 * 1048576),
-    "A9 adjoint of z=a*b+c*d": ("k_adjoint_lazy<E1,MathDF>", (755.3 + 550.5) * 1e6,
-                                1296 * 1048576),
-}
+TRAFFIC_32 = {}
 
 
 def traffic_bytes(row_name, nbytes):

@@ -280,7 +280,8 @@ int su3s_set_pipeline(int mode);
 /* Read and clear the library's device error word (a stream-ordered copy
  * followed by a synchronisation of `stream`): 0 if every bounded wait inside
  * the library's kernels completed since the last call, 1 if a TMA pipeline
- * wait gave up (its results are then incomplete). */
+ * wait gave up, 2 if a staged kernel found its shared memory misaligned for
+ * tensor copies and staged nothing (results are incomplete in both cases). */
 int su3s_device_error(int* code, void* stream);
 
 /* Autotune the launch geometry for `e` into `dest`: times each candidate

@@ -150,8 +150,18 @@ static bool find_geometry(const void* kernel, int64_t nvec, int nmu, Geo* g) {
   return true;
 }
 
+// Whether the staged kernels can read field f: 32 sites of a component
+// contiguous, and (matrices, vectors) a tensor map.
 bool tma_layout_ok(const su3s_field* f) {
-  return f->layout == SU3S_SOA || f->block >= 32;
+  if (f->layout != SU3S_SOA && f->block < 32) return false;
+  return f->kind == SU3S_REAL || f->tmap_ok;
+}
+
+// ... for every leaf of a canonical tree and the destination.
+bool tma_tree_ok(const Canon& c, const su3s_field* dest) {
+  bool ok = tma_layout_ok(dest);
+  for (const su3s_field* f : c.leaves) ok = ok && tma_layout_ok(f);
+  return ok;
 }
 
 // Occupancy of a staged kernel (blocks per SM), cached per (kernel, threads).
@@ -322,6 +332,8 @@ static void fill_desc(su3s_field* f) {
     d.s_c = f->Vpad;
     d.s_mu = nc * f->Vpad;
     d.s_blk = 0;
+    d.row_blk = 0;
+    d.row_mu = (int32_t)nc;
   } else {
     int lb = 0;
     while ((1 << lb) < f->block) ++lb;
@@ -330,7 +342,56 @@ static void fill_desc(su3s_field* f) {
     d.s_c = f->block;
     d.s_mu = nc * f->block;
     d.s_blk = (int64_t)f->nmu * nc * f->block;
+    d.row_blk = (int32_t)(f->nmu * nc);
+    d.row_mu = (int32_t)nc;
   }
+}
+
+// ---------------------------------------------------------- tensor maps
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library); null when no driver is present.
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();  // clear the lookup's error
+  });
+  return fn;
+}
+
+// Tensor map of an FP64 matrix or vector field for the staged kernels: a 2-D
+// tensor of rows of s_c complex elements (2 s_c doubles; s_c = Vpad in the SoA
+// layout, the site block otherwise), rows s_c * 16 bytes apart; the box is
+// one 32-site tile (64 doubles) of every component of one object.
+static void encode_tmap(su3s_field* f) {
+  f->tmap_ok = false;
+  memset(&f->tmap, 0, sizeof f->tmap);
+  if ((f->prec != SU3S_F64 && f->prec != SU3S_F64_C12) || f->kind == SU3S_REAL) return;
+  if (f->layout == SU3S_AOSOA && f->block < 32) return;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return;
+  const uint64_t w = (uint64_t)f->desc.s_c;
+  const uint64_t rows = (uint64_t)f->Vpad * f->nmu * f->ncomp / w;
+  const cuuint64_t dims[2] = {2 * w, rows};
+  const cuuint64_t strides[1] = {w * 16};
+  const cuuint32_t box[2] = {64, (cuuint32_t)f->ncomp};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(&f->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, f->ptr, dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  f->tmap_ok = r == CUDA_SUCCESS;
 }
 
 // ------------------------------------------------------------- canonical
@@ -422,7 +483,10 @@ static void split_scalar(double s, float* h, float* l) {
 
 int build_params(const Canon& c, const su3s_field* dest, int vps, KParams* p) {
   memset(p, 0, sizeof *p);
-  for (size_t i = 0; i < c.leaves.size(); ++i) p->leaf[i] = c.leaves[i]->desc;
+  for (size_t i = 0; i < c.leaves.size(); ++i) {
+    p->leaf[i] = c.leaves[i]->desc;
+    p->tm[i] = c.leaves[i]->tmap;
+  }
   p->dst = dest->desc;
   for (size_t k = 0; k < c.scalars.size(); ++k) {
     p->sc[k] = c.scalars[k];
@@ -474,7 +538,7 @@ static int do_eval(su3s_field* dest, const su3s_expr* e, int math, cudaStream_t 
   KParams p;
   build_params(c, dest, ent->vps, &p);
   Launch L;
-  plan_launch(ent, p.nvec, p.nmu, tma_layout_ok(dest), &L);
+  plan_launch(ent, p.nvec, p.nmu, tma_tree_ok(c, dest), &L);
   cudaError_t ce = L.fn(&p, L.grid, L.block, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "evaluation kernel launch");
   return ok();
@@ -553,6 +617,7 @@ SU3S_EXPORT int su3s_field_wrap(const su3s_lattice* lat, int kind, int nmu, int 
   f->ptr = dev_ptr;
   f->bytes = bytes;
   fill_desc(f);
+  encode_tmap(f);
   *out = f;
   return ok();
 }
@@ -823,7 +888,7 @@ SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* 
   if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s", c.sig.c_str());
   KParams p;
   build_params(c, dest, ent->vps, &p);
-  return tune_entry(ent, &p, p.nvec, p.nmu, tma_layout_ok(dest), (cudaStream_t)stream,
+  return tune_entry(ent, &p, p.nvec, p.nmu, tma_tree_ok(c, dest), (cudaStream_t)stream,
                     threads_out, bps_out, variant_out, best_ms);
 }
 
@@ -878,9 +943,8 @@ static int prepare_adjoint(const su3s_expr* e, const su3s_field* gout, su3s_fiel
   p->gout = gout->desc;
   for (size_t i = 0; i < c.leaves.size(); ++i)
     if (gleaves && gleaves[i]) p->gleaf[i] = gleaves[i]->desc;
-  *tma = tma_layout_ok(gout);
-  for (size_t i = 0; i < c.leaves.size(); ++i)
-    if (gleaves && gleaves[i]) *tma = *tma && tma_layout_ok(gleaves[i]);
+  p->tm_gout = gout->tmap;
+  *tma = tma_tree_ok(c, gout);   // leaves and dL/dZ are staged; gradients are stored per site
   return SU3S_OK;
 }
 

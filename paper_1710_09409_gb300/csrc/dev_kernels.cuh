@@ -256,9 +256,12 @@ __global__ void __launch_bounds__(256) k_adjoint(const __grid_constant__ GParams
 // ------------------------------------------------- TMA-staged variants
 // FP64 storage.  Each warp owns a 32-site tile buffer in shared memory: it
 // waits for its tile, reads its sites into registers, immediately asks the
-// TMA engine for the next tile (one elected lane issues one bulk copy per leaf
-// component: 32 sites x 16 bytes, contiguous in both layouts when the site
-// block is >= 32), and computes while the copy is in flight.
+// TMA engine for the next tile, and computes while the copy is in flight.
+// One lane issues one 2-D tensor copy per matrix or vector object: the
+// field's tensor map has rows of 32 consecutive sites of one component
+// (64 doubles; rows of one object are Vpad apart in the SoA layout and the
+// site block apart in the site-blocked one), so an object's tile is a box of
+// (components x 64 doubles) landing as [component][site] in shared memory.
 
 template <int K, int PREC>
 struct StageBytes {
@@ -283,63 +286,53 @@ struct TileBytes {
                                (GRAD ? StageBytes<Tree::kind, PREC>::value : 0);
 };
 
-// Copies of one tile: every (leaf, component) segment is one bulk copy; the
-// warp's lanes issue them in parallel, lane j taking copy j (and j+32, ...).
-// Copies are numbered leaf by leaf; dL/dZ (reverse mode) comes last.
+// Shared memory of one warp in the whole-tile variant: the tile, then its
+// barrier, padded so every warp's buffer starts on a 128-byte boundary.
+__host__ __device__ constexpr int tma_warp_stride(int tile_bytes) {
+  return (tile_bytes + 16 + 127) / 128 * 128;
+}
+
+// Stage one object (kind K) of the 32-site tile starting at site s0, link mu,
+// into dst (one lane): matrix and vector objects are one 2-D tensor copy of
+// all their components (rows of the field's tensor map), real objects one
+// 256-byte bulk copy.
 template <int K, int PREC>
-struct NCopies {
-  static constexpr int value = K == KR ? 1 : StageBytes<K, PREC>::value / 512;
-};
-
-template <class Tree, int PREC, int I>
-struct CopyBase {
-  static constexpr int value =
-      CopyBase<Tree, PREC, I - 1>::value + NCopies<LeafKind<Tree, I - 1>::value, PREC>::value;
-};
-template <class Tree, int PREC>
-struct CopyBase<Tree, PREC, 0> {
-  static constexpr int value = 0;
-};
-
-// Issue copy number j if it belongs to object (kind K, first copy J0).
-template <int K, int PREC, int J0>
-__device__ __forceinline__ void issue_if_mine(int j, const FieldDesc& f, int64_t s0, int mu,
-                                              unsigned char* dst, uint64_t* bar) {
-  constexpr int N = NCopies<K, PREC>::value;
-  const int c = j - J0;
-  if (c >= 0 && c < N) {
-    const int64_t e = elem_base(f, s0, mu) + (int64_t)c * f.s_c;
-    if constexpr (K == KR) tma_load_1d(dst, (const char*)f.ptr + e * 8, 256, bar);
-    else tma_load_1d(dst + c * 512, (const char*)f.ptr + e * 16, 512, bar);
+__device__ __forceinline__ void issue_obj(const FieldDesc& f, const CUtensorMap* tm, int64_t s0,
+                                          int mu, unsigned char* dst, uint64_t* bar) {
+  if constexpr (K == KR) {
+    const int64_t e = elem_base(f, s0, mu);
+    tma_load_1d(dst, (const char*)f.ptr + e * 8, 256, bar);
+  } else {
+    const int x = 2 * (int)(s0 & (int64_t)f.mask);  // column in doubles: 16-byte aligned
+    const int y = (int)((s0 >> f.logB) * f.row_blk + (int64_t)mu * f.row_mu);
+    tma_load_2d(dst, tm, x, y, bar);
   }
 }
 
 template <class Tree, int I, int PREC>
-__device__ __forceinline__ void issue_leaves_j(int j, const KParams& p, int64_t s0, int mu,
-                                               unsigned char* buf, uint64_t* bar) {
+__device__ __forceinline__ void issue_leaves(const KParams& p, int64_t s0, int mu,
+                                             unsigned char* buf, uint64_t* bar) {
   if constexpr (I < Tree::nleaf) {
-    issue_if_mine<LeafKind<Tree, I>::value, PREC, CopyBase<Tree, PREC, I>::value>(
-        j, p.leaf[I], s0, mu, buf + LeafOff<Tree, PREC, I>::value, bar);
-    issue_leaves_j<Tree, I + 1, PREC>(j, p, s0, mu, buf, bar);
+    issue_obj<LeafKind<Tree, I>::value, PREC>(p.leaf[I], &p.tm[I], s0, mu,
+                                              buf + LeafOff<Tree, PREC, I>::value, bar);
+    issue_leaves<Tree, I + 1, PREC>(p, s0, mu, buf, bar);
   }
 }
 
-// Whole warp: expect the tile's bytes (lane 0), then issue its copies.
+// Whole tile: one lane arms the barrier with the tile's bytes and issues one
+// copy per object (dL/dZ last in reverse mode).
 template <class Tree, int PREC, bool GRAD>
 __device__ __forceinline__ void issue_tile(int lane, const KParams& p, const FieldDesc* gout,
-                                           int64_t s0, int mu, unsigned char* buf, uint64_t* bar) {
+                                           const CUtensorMap* tm_gout, int64_t s0, int mu,
+                                           unsigned char* buf, uint64_t* bar) {
   constexpr int NL = Tree::nleaf;
-  constexpr int NJ = CopyBase<Tree, PREC, NL>::value + (GRAD ? NCopies<Tree::kind, PREC>::value : 0);
-  if (lane == 0) mbar_arrive_expect_tx(bar, TileBytes<Tree, PREC, GRAD>::value);
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < (NJ + 31) / 32; ++r) {
-    const int j = lane + 32 * r;
-    issue_leaves_j<Tree, 0, PREC>(j, p, s0, mu, buf, bar);
+  if (lane == 0) {
+    mbar_arrive_expect_tx(bar, TileBytes<Tree, PREC, GRAD>::value);
+    issue_leaves<Tree, 0, PREC>(p, s0, mu, buf, bar);
     if constexpr (GRAD)
-      issue_if_mine<Tree::kind, PREC, CopyBase<Tree, PREC, NL>::value>(
-          j, *gout, s0, mu, buf + LeafOff<Tree, PREC, NL>::value, bar);
+      issue_obj<Tree::kind, PREC>(*gout, tm_gout, s0, mu, buf + LeafOff<Tree, PREC, NL>::value, bar);
   }
+  __syncwarp();
 }
 
 // Read this lane's site of a staged object into ctx.leaf[slot].
@@ -377,7 +370,7 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
   constexpr int W = Width<Tree::kind>::value;
   constexpr int TB = TileBytes<Tree, PREC, false>::value;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* buf = smem + warp * (TB + 16);
+  unsigned char* buf = smem + warp * tma_warp_stride(TB);
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf + TB);
   const int mu = blockIdx.y;
   const int64_t ntiles = rg.end;
@@ -388,7 +381,7 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
     fence_barrier_init();
   }
   __syncwarp();
-  if (t < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, t << 5, mu, buf, bar);
+  if (t < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, nullptr, t << 5, mu, buf, bar);
   Ctx<M, NL, NS> ctx;
 #pragma unroll
   for (int k = 0; k < (NS > 0 ? NS : 1); ++k) ctx.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
@@ -404,7 +397,7 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
     fence_proxy_async_smem();
     __syncwarp();
     const int64_t tn = t + wstride;
-    if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, tn << 5, mu, buf, bar);
+    if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, nullptr, tn << 5, mu, buf, bar);
     typename M::A acc[1][W];
     if constexpr (Tree::accumulates) {
       acc_into<Tree, M, true, 1>(ctx, acc[0]);
@@ -421,7 +414,8 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
 
 template <class Tree, class M, int PREC>
 __global__ void __launch_bounds__(256) k_eval_tma(const __grid_constant__ KParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!smem_aligned(smem, p.err)) return;
   tma_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);
 }
 
@@ -432,7 +426,7 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
   constexpr int TB = TileBytes<Tree, P_F64, true>::value;
   constexpr int GOFF = LeafOff<Tree, P_F64, NL>::value;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* buf = smem + warp * (TB + 16);
+  unsigned char* buf = smem + warp * tma_warp_stride(TB);
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf + TB);
   const int mu = blockIdx.y;
   const int64_t ntiles = rg.end;
@@ -443,7 +437,7 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
     fence_barrier_init();
   }
   __syncwarp();
-  if (t < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, t << 5, mu, buf, bar);
+  if (t < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, &p.tm_gout, t << 5, mu, buf, bar);
   Ctx<M, NL, NS> ctx;
 #pragma unroll
   for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
@@ -462,7 +456,7 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
     fence_proxy_async_smem();
     __syncwarp();
     const int64_t tn = t + wstride;
-    if (tn < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, tn << 5, mu, buf, bar);
+    if (tn < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, &p.tm_gout, tn << 5, mu, buf, bar);
     GradAcc<M, NL> ga;
 #pragma unroll
     for (int i = 0; i < NL; ++i)
@@ -477,7 +471,8 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
 
 template <class Tree, class M>
 __global__ void __launch_bounds__(256) k_adjoint_tma(const __grid_constant__ GParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!smem_aligned(smem, p.k.err)) return;
   adj_tma_range<Tree, M>(p, warp_range(p.k.nvec >> 5), smem);
 }
 
@@ -529,7 +524,7 @@ struct LazyLayout {
   static constexpr int NB = NL + (GRAD ? 1 : 0);   // barriers
   static constexpr int DATA = TileBytes<Tree, PREC, GRAD>::value;
   static constexpr int BYTES = DATA + 8 * NB;      // + one barrier per buffer
-  static constexpr int STRIDE = (BYTES + 15) / 16 * 16;
+  static constexpr int STRIDE = (BYTES + 127) / 128 * 128;
 };
 
 template <class Tree, class M, int PREC, bool GRAD>
@@ -541,6 +536,7 @@ struct LazyCtx {
   uint64_t* bars;
   const KParams* p;
   const FieldDesc* gout;
+  const CUtensorMap* tm_gout;
   int64_t next_s0;
   int mu, lane;
   uint32_t parity;
@@ -552,10 +548,13 @@ struct LazyCtx {
   __device__ __forceinline__ void issue(int64_t s0) const {
     constexpr int K = I < NL ? LeafKind<Tree, I>::value : Tree::kind;
     constexpr int OFF = LeafOff<Tree, PREC, I>::value;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[I], StageBytes<K, PREC>::value);
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&bars[I], StageBytes<K, PREC>::value);
+      const FieldDesc& f = I < NL ? p->leaf[I < NL ? I : 0] : *gout;
+      const CUtensorMap* tm = I < NL ? &p->tm[I < NL ? I : 0] : tm_gout;
+      issue_obj<K, PREC>(f, tm, s0, mu, buf + OFF, &bars[I]);
+    }
     __syncwarp();
-    const FieldDesc& f = I < NL ? p->leaf[I < NL ? I : 0] : *gout;
-    issue_if_mine<K, PREC, 0>(lane, f, s0, mu, buf + OFF, &bars[I]);
   }
 
   // wait for leaf I of the current tile (bounded; a time-out marks the warp dead)
@@ -618,7 +617,8 @@ struct LazyCtx {
 
 template <class Tree, class M, int PREC, bool GRAD>
 __device__ __forceinline__ void lazy_setup(LazyCtx<Tree, M, PREC, GRAD>& c, unsigned char* smem,
-                                           const KParams& p, const FieldDesc* gout) {
+                                           const KParams& p, const FieldDesc* gout,
+                                           const CUtensorMap* tm_gout) {
   using L = LazyLayout<Tree, PREC, GRAD>;
   const int warp = threadIdx.x >> 5;
   c.lane = threadIdx.x & 31;
@@ -626,6 +626,7 @@ __device__ __forceinline__ void lazy_setup(LazyCtx<Tree, M, PREC, GRAD>& c, unsi
   c.bars = reinterpret_cast<uint64_t*>(c.buf + L::DATA);
   c.p = &p;
   c.gout = gout;
+  c.tm_gout = tm_gout;
   c.mu = blockIdx.y;
   c.parity = 0;
   c.dead = false;
@@ -644,7 +645,7 @@ template <class Tree, class M, int PREC>
 __device__ __forceinline__ void lazy_range(const KParams& p, Range rg, unsigned char* smem) {
   constexpr int W = Width<Tree::kind>::value;
   LazyCtx<Tree, M, PREC, false> c;
-  lazy_setup(c, smem, p, nullptr);
+  lazy_setup(c, smem, p, nullptr, nullptr);
   const int64_t ntiles = rg.end;
   const int64_t wstride = rg.stride;
   int64_t t = rg.first;
@@ -673,7 +674,8 @@ __device__ __forceinline__ void lazy_range(const KParams& p, Range rg, unsigned 
 
 template <class Tree, class M, int PREC>
 __global__ void __launch_bounds__(128, 4) k_eval_lazy(const __grid_constant__ KParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!smem_aligned(smem, p.err)) return;
   lazy_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);
 }
 
@@ -682,7 +684,7 @@ __device__ __forceinline__ void adj_lazy_range(const GParams& p, Range rg, unsig
   constexpr int NL = Tree::nleaf;
   constexpr int W = Width<Tree::kind>::value;
   LazyCtx<Tree, M, P_F64, true> c;
-  lazy_setup(c, smem, p.k, &p.gout);
+  lazy_setup(c, smem, p.k, &p.gout, &p.tm_gout);
   const int64_t ntiles = rg.end;
   const int64_t wstride = rg.stride;
   int64_t t = rg.first;
@@ -711,7 +713,8 @@ __device__ __forceinline__ void adj_lazy_range(const GParams& p, Range rg, unsig
 
 template <class Tree, class M>
 __global__ void __launch_bounds__(128, 3) k_adjoint_lazy(const __grid_constant__ GParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!smem_aligned(smem, p.k.err)) return;
   adj_lazy_range<Tree, M>(p, warp_range(p.k.nvec >> 5), smem);
 }
 
@@ -862,7 +865,7 @@ struct RingLayout {
   static constexpr int K = NOBJ > 3 ? 3 : NOBJ;                   // buffers per warp
   static constexpr int BUF = StageBytes<KM, PREC>::value;         // largest object
   static constexpr int DATA = K * BUF;
-  static constexpr int STRIDE = (DATA + 8 * K + 15) / 16 * 16;
+  static constexpr int STRIDE = (DATA + 8 * K + 127) / 128 * 128;
 };
 
 template <class Tree, class M, int PREC, bool GRAD>
@@ -876,6 +879,7 @@ struct RingCtx {
   uint64_t* bars;
   const KParams* p;
   const FieldDesc* gout;
+  const CUtensorMap* tm_gout;
   int64_t cur_s0, next_s0;
   int mu, lane;
   mutable uint32_t ph;  // barrier parity of each buffer
@@ -886,10 +890,13 @@ struct RingCtx {
   template <int I>
   __device__ __forceinline__ void issue(int64_t s0, int b) const {
     constexpr int K = I < NL ? LeafKind<Tree, (I < NL ? I : 0)>::value : Tree::kind;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[b], StageBytes<K, PREC>::value);
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&bars[b], StageBytes<K, PREC>::value);
+      const FieldDesc& f = I < NL ? p->leaf[I < NL ? I : 0] : *gout;
+      const CUtensorMap* tm = I < NL ? &p->tm[I < NL ? I : 0] : tm_gout;
+      issue_obj<K, PREC>(f, tm, s0, mu, buf + b * L::BUF, &bars[b]);
+    }
     __syncwarp();
-    const FieldDesc& f = I < NL ? p->leaf[I < NL ? I : 0] : *gout;
-    issue_if_mine<K, PREC, 0>(lane, f, s0, mu, buf + b * L::BUF, &bars[b]);
   }
 
   // issue the object at position j of the tile whose first site is s0
@@ -942,7 +949,8 @@ struct RingCtx {
 
 template <class Tree, class M, int PREC, bool GRAD>
 __device__ __forceinline__ void ring_setup(RingCtx<Tree, M, PREC, GRAD>& c, unsigned char* smem,
-                                           const KParams& p, const FieldDesc* gout) {
+                                           const KParams& p, const FieldDesc* gout,
+                                           const CUtensorMap* tm_gout) {
   using L = RingLayout<Tree, PREC, GRAD>;
   const int warp = threadIdx.x >> 5;
   c.lane = threadIdx.x & 31;
@@ -950,6 +958,7 @@ __device__ __forceinline__ void ring_setup(RingCtx<Tree, M, PREC, GRAD>& c, unsi
   c.bars = reinterpret_cast<uint64_t*>(c.buf + L::DATA);
   c.p = &p;
   c.gout = gout;
+  c.tm_gout = tm_gout;
   c.mu = blockIdx.y;
   c.ph = 0;
   c.dead = false;
@@ -968,7 +977,7 @@ template <class Tree, class M, int PREC>
 __device__ __forceinline__ void ring_range(const KParams& p, Range rg, unsigned char* smem) {
   constexpr int W = Width<Tree::kind>::value;
   RingCtx<Tree, M, PREC, false> c;
-  ring_setup(c, smem, p, nullptr);
+  ring_setup(c, smem, p, nullptr, nullptr);
   const int64_t ntiles = rg.end;
   int64_t t = rg.first;
   if (t < ntiles) c.template issue_first<0>(t << 5);
@@ -995,7 +1004,8 @@ __device__ __forceinline__ void ring_range(const KParams& p, Range rg, unsigned 
 
 template <class Tree, class M, int PREC>
 __global__ void __launch_bounds__(128, 4) k_eval_ring(const __grid_constant__ KParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!smem_aligned(smem, p.err)) return;
   ring_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);
 }
 
@@ -1004,7 +1014,7 @@ __device__ __forceinline__ void adj_ring_range(const GParams& p, Range rg, unsig
   constexpr int NL = Tree::nleaf;
   constexpr int W = Width<Tree::kind>::value;
   RingCtx<Tree, M, P_F64, true> c;
-  ring_setup(c, smem, p.k, &p.gout);
+  ring_setup(c, smem, p.k, &p.gout, &p.tm_gout);
   const int64_t ntiles = rg.end;
   int64_t t = rg.first;
   if (t < ntiles) c.template issue_first<0>(t << 5);
@@ -1031,7 +1041,8 @@ __device__ __forceinline__ void adj_ring_range(const GParams& p, Range rg, unsig
 
 template <class Tree, class M>
 __global__ void __launch_bounds__(128, 3) k_adjoint_ring(const __grid_constant__ GParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!smem_aligned(smem, p.k.err)) return;
   adj_ring_range<Tree, M>(p, warp_range(p.k.nvec >> 5), smem);
 }
 
@@ -1052,7 +1063,9 @@ cudaError_t launch_adjoint(const void* params, dim3 grid, dim3 block, cudaStream
 
 // Dynamic shared memory of a TMA-staged launch: one tile buffer and one
 // barrier per warp.
-inline size_t tma_smem(int tile_bytes, dim3 block) { return (size_t)(block.x / 32) * (tile_bytes + 16); }
+inline size_t tma_smem(int tile_bytes, dim3 block) {
+  return (size_t)(block.x / 32) * tma_warp_stride(tile_bytes);
+}
 
 template <class Tree, class M, int PREC>
 cudaError_t launch_eval_tma(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
@@ -1061,7 +1074,8 @@ cudaError_t launch_eval_tma(const void* params, dim3 grid, dim3 block, cudaStrea
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_eval_tma<Tree, M, PREC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * (TB + 16));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * tma_warp_stride(TB));
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -1076,7 +1090,8 @@ cudaError_t launch_adjoint_tma(const void* params, dim3 grid, dim3 block, cudaSt
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_adjoint_tma<Tree, M>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * (TB + 16));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * tma_warp_stride(TB));
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -1181,64 +1196,20 @@ struct Sig<Adj<X>> {
 // Registry hooks implemented by the library (api.cu).  A TMA-staged variant
 // (null for reduced-precision storage) is registered beside the plain one,
 // with its tile bytes per warp.
-// Shape predicates of a tree used to pick its default launch.
-template <class T, int I>
-struct AnyRepeat {
-  static constexpr bool value = Count<T, I>::value > 1 || AnyRepeat<T, I - 1>::value;
-};
-template <class T>
-struct AnyRepeat<T, -1> {
-  static constexpr bool value = false;
-};
-template <class T>
-struct IsProd {
-  static constexpr bool value = false;
-};
-template <class X, class Y>
-struct IsProd<Mul<X, Y>> {
-  static constexpr bool value = Operand<X>::base::is_leaf && Operand<Y>::base::is_leaf;
-};
-template <int K, class X>
-struct IsProd<Scale<K, X>> {
-  static constexpr bool value = IsProd<X>::value;
-};
-template <class T>
-struct IsSumOfProds {
-  static constexpr bool value = false;
-};
-template <class X, class Y>
-struct IsSumOfProds<Add<X, Y>> {
-  static constexpr bool value = IsProd<X>::value && IsProd<Y>::value;
-};
-template <class X, class Y>
-struct IsSumOfProds<Sub<X, Y>> {
-  static constexpr bool value = IsProd<X>::value && IsProd<Y>::value;
-};
 // Default launch of a tree when the caller set none: data movement variant,
 // threads per block, blocks per SM (0: as many as fit, or one site per thread
-// for plain loads).  The rules restate the fastest candidates of the autotuner
-// (su3s_tune, su3s_tune_adjoint) on the GB300 at 48^4 and 32^4, FP64 storage.
+// for plain loads).  The rule restates the fastest candidates of the
+// autotuner (su3s_tune, su3s_tune_adjoint) on the GB300 at 48^4, FP64 storage;
+// trees without staged kernels (reduced precisions) always use plain loads.
 struct DefaultGeo {
   int variant, threads, bps;
 };
 template <class Tree, class M, bool GRAD>
 constexpr DefaultGeo default_geometry() {
-  constexpr bool repeat = AnyRepeat<Tree, Tree::nleaf - 1>::value;
-  constexpr bool small = Tree::nleaf <= 2;
-  constexpr bool sum_of_prods = IsSumOfProds<Tree>::value;
-  if constexpr (M::kScaled) {
-    // fixed point: integer latency favours many small blocks with plain loads
-    // for products; sums of products stage whole tiles
-    if (repeat) return DefaultGeo{0, 64, 0};
-    if (small) return GRAD ? DefaultGeo{0, 64, 0} : DefaultGeo{0, 64, 0};
-    if (sum_of_prods) return GRAD ? DefaultGeo{1, 128, 4} : DefaultGeo{1, 256, 2};
-    return DefaultGeo{1, 128, 2};
-  } else {
-    if (repeat) return DefaultGeo{0, 64, 0};
-    if (small) return DefaultGeo{1, 256, 4};
-    if (sum_of_prods) return GRAD ? DefaultGeo{2, 64, 0} : DefaultGeo{0, 64, 0};
-    return DefaultGeo{2, 128, 0};
-  }
+  // With one tensor copy per object, whole-tile staging is the fastest data
+  // movement for every FP64 tree measured, in both FP64-accurate arithmetics
+  if constexpr (M::kScaled) return DefaultGeo{1, 128, 0};
+  else return DefaultGeo{1, 256, 0};
 }
 
 // Kernel variants of one tree: 0 plain loads, 1 TMA-staged eagerly (whole
@@ -1263,7 +1234,7 @@ void reg_eval(int math) {
   if constexpr (PREC == P_F64 || PREC == P_F64_C12) {
     v.fn[1] = &launch_eval_tma<Tree, M, PREC>;
     v.kernel[1] = (const void*)&k_eval_tma<Tree, M, PREC>;
-    v.warp_bytes[1] = TileBytes<Tree, PREC, false>::value + 16;
+    v.warp_bytes[1] = tma_warp_stride(TileBytes<Tree, PREC, false>::value);
     v.fn[2] = &launch_eval_lazy<Tree, M, PREC>;
     v.kernel[2] = (const void*)&k_eval_lazy<Tree, M, PREC>;
     v.warp_bytes[2] = LazyLayout<Tree, PREC, false>::STRIDE;
@@ -1287,7 +1258,7 @@ void reg_adjoint(int math) {
   v.kernel[0] = (const void*)&k_adjoint<Tree, M>;
   v.fn[1] = &launch_adjoint_tma<Tree, M>;
   v.kernel[1] = (const void*)&k_adjoint_tma<Tree, M>;
-  v.warp_bytes[1] = TileBytes<Tree, P_F64, true>::value + 16;
+  v.warp_bytes[1] = tma_warp_stride(TileBytes<Tree, P_F64, true>::value);
   v.fn[2] = &launch_adjoint_lazy<Tree, M>;
   v.kernel[2] = (const void*)&k_adjoint_lazy<Tree, M>;
   v.warp_bytes[2] = LazyLayout<Tree, P_F64, true>::STRIDE;

@@ -7,16 +7,28 @@
 // more (again bounded) for its own copies in flight, and leaves its loop.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace su3s {
 
-constexpr uint32_t kTmaSpinLimit = 1u << 24;
-constexpr int kErrTmaTimeout = 1;
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t smem_u32_base(const void* p) { return smem_u32(p); }
+
+constexpr uint32_t kTmaSpinLimit = 1u << 24;
+constexpr int kErrTmaTimeout = 1;
+constexpr int kErrSmemAlign = 2;   // dynamic shared memory not 128-byte aligned: nothing staged
+
+// Tensor copies need 128-byte aligned shared-memory destinations; a kernel
+// whose dynamic shared memory is not aligned records the fact and stages
+// nothing (all its warps return before any copy).
+__device__ __forceinline__ bool smem_aligned(const void* smem, int* err) {
+  if ((smem_u32_base(smem) & 127u) == 0) return true;
+  if (err && threadIdx.x == 0) atomicExch(err, kErrSmemAlign);
+  return false;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -48,6 +60,18 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 2-D tensor copy global -> shared of the map's box at column x, row y,
+// completion counted on `bar` in bytes.  dst 128-byte aligned; x times the
+// element size a multiple of 16 bytes; the map lives in kernel parameter space.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
 

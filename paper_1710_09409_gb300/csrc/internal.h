@@ -26,6 +26,8 @@ struct su3s_field {
   void* ptr;
   size_t bytes;
   su3s::FieldDesc desc;
+  CUtensorMap tmap;   // rows of 32-site tiles for the staged kernels (FP64 complex fields)
+  bool tmap_ok;       // tmap was encoded
 };
 
 struct su3s_expr {
@@ -89,6 +91,7 @@ void set_geometry(const void* kernel, int64_t nvec, int nmu, int threads, int bl
 // resolve variant + geometry for an entry; tma_ok: the fields allow 32-site tiles
 int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* out);
 bool tma_layout_ok(const su3s_field* f);
+bool tma_tree_ok(const Canon& c, const su3s_field* dest);
 
 // fill a KParams from a canonical tree and destination
 int build_params(const Canon& c, const su3s_field* dest, int vps, KParams* p);

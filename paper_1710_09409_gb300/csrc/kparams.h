@@ -1,6 +1,7 @@
 // Plain-data kernel parameters shared by host planning code and kernels.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only)
 #include <stdint.h>
 
 namespace su3s {
@@ -22,9 +23,18 @@ struct FieldDesc {
   int64_t s_c;
   int32_t logB;
   uint32_t mask;
+  // the same addressing in rows of s_c elements (the rows of the field's
+  // 2-D tensor map): component 0 of (s, mu) starts row
+  //   (s >> logB) * row_blk + mu * row_mu, at column s & mask
+  int32_t row_blk;
+  int32_t row_mu;
 };
 
 struct KParams {
+  // 2-D tensor maps of the leaves (FP64 matrix and vector fields whose
+  // 32-site tiles are rows of a 2-D tensor): one tile of all components of an
+  // object is one tensor copy.  Valid where the staged kernels run.
+  CUtensorMap tm[kMaxLeaves];
   FieldDesc leaf[kMaxLeaves];
   FieldDesc dst;
   double sc[kMaxScalars];   // real factors of scale nodes, in tree order
@@ -39,6 +49,7 @@ struct KParams {
 // written (ptr == nullptr: skipped).
 struct GParams {
   KParams k;                  // leaves, scalars, sizes (k.dst unused)
+  CUtensorMap tm_gout;        // tensor map of dL/dZ
   FieldDesc gout;             // dL/dZ
   FieldDesc gleaf[kMaxLeaves];
 };
