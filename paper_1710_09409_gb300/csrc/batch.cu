@@ -64,6 +64,73 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BItem* __restrict__ item
   }
 }
 
+// A 32-site tile of one item for the staged kernel.
+struct BWTile {
+  int32_t item;
+  int32_t mu;
+  int64_t s0;
+};
+
+// Staged persistent kernel: every warp takes a contiguous run of the list of
+// 32-site tiles of all items (so consecutive tiles mostly share an item and
+// its descriptors stay in L1) and walks it with the whole-tile TMA pipeline of
+// the single-lattice kernels: one tensor copy per object, the next tile's
+// copies in flight while the current one is computed.  Tensor maps and
+// descriptors are read from the item table in global memory.
+template <class M, class Tree>
+__global__ void __launch_bounds__(256) k_batch_tma(const BItem* __restrict__ items,
+                                                   const BWTile* __restrict__ wt, int64_t n,
+                                                   int* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!smem_aligned(smem, err)) return;
+  constexpr int NL = Tree::nleaf;
+  constexpr int NS = Tree::nsc;
+  constexpr int W = Width<Tree::kind>::value;
+  constexpr int TB = TileBytes<Tree, P_F64, false>::value;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* buf = smem + warp * tma_warp_stride(TB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf + TB);
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t chunk = (n + nwarps - 1) / nwarps;
+  int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * chunk;
+  const int64_t end = i + chunk < n ? i + chunk : n;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  if (i < end) {
+    const BWTile T = wt[i];
+    issue_tile<Tree, P_F64, false>(lane, items[T.item].k, nullptr, nullptr, T.s0, T.mu, buf, bar);
+  }
+  uint32_t phase = 0;
+  Ctx<M, NL, NS> ctx;
+  while (i < end) {
+    const BWTile T = wt[i];
+    const KParams& p = items[T.item].k;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase));
+    if (!ok) {
+      if (lane == 0) report_timeout(err, bar, phase);
+      break;
+    }
+    phase ^= 1;
+    read_leaves<Tree, 0, P_F64, M>(buf, lane, ctx);
+    fence_proxy_async_smem();
+    __syncwarp();
+    const int64_t in = i + 1;
+    if (in < end) {
+      const BWTile Tn = wt[in];
+      issue_tile<Tree, P_F64, false>(lane, items[Tn.item].k, nullptr, nullptr, Tn.s0, Tn.mu, buf, bar);
+    }
+#pragma unroll
+    for (int k = 0; k < (NS > 0 ? NS : 1); ++k) ctx.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
+    typename M::A acc[1][W];
+    acc_into<Tree, M, true, 1>(ctx, acc[0]);
+    store_obj<Tree::kind, P_F64, M, 1, W>(p.dst, T.s0 + lane, T.mu, acc);
+    i = in;
+  }
+}
+
 // Persistent kernel of batch tree `tree` in arithmetic M.
 template <class M>
 static const void* batch_kernel(int tree) {
@@ -85,6 +152,31 @@ static const void* batch_kernel(int math, int tree) {
                            : batch_kernel<MathDF>(tree);
 }
 
+// Staged persistent kernel of batch tree `tree` and its tile bytes per warp.
+template <class M, class Tree>
+static const void* staged_entry(int* warp_bytes) {
+  *warp_bytes = tma_warp_stride(TileBytes<Tree, P_F64, false>::value);
+  return (const void*)&k_batch_tma<M, Tree>;
+}
+template <class M>
+static const void* batch_kernel_tma(int tree, int* warp_bytes) {
+  switch (tree) {
+    case 0: return staged_entry<M, cat::MM>(warp_bytes);
+    case 1: return staged_entry<M, cat::E1>(warp_bytes);
+    case 2: return staged_entry<M, cat::MV>(warp_bytes);
+    case 3: return staged_entry<M, cat::E2>(warp_bytes);
+    case 4: return staged_entry<M, cat::E3>(warp_bytes);
+    case 5: return staged_entry<M, cat::MMM>(warp_bytes);
+    case 6: return staged_entry<M, cat::E1Lin>(warp_bytes);
+    default: return staged_entry<M, cat::AdjMM>(warp_bytes);
+  }
+}
+static const void* batch_kernel_tma(int math, int tree, int* warp_bytes) {
+  return math == MATH_F64  ? batch_kernel_tma<MathF64>(tree, warp_bytes)
+         : math == MATH_FX ? batch_kernel_tma<MathFX>(tree, warp_bytes)
+                           : batch_kernel_tma<MathDF>(tree, warp_bytes);
+}
+
 }  // namespace su3s
 
 using namespace su3s;
@@ -98,6 +190,7 @@ struct su3s_batch {
   bool built = false;
   BItem* d_items = nullptr;
   BTile* d_tiles = nullptr;
+  BWTile* d_wtiles = nullptr;   // 32-site tiles of the staged items
   int64_t ntiles = 0, nsites = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -108,10 +201,12 @@ static void batch_release(su3s_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_wtiles) cudaFree(b->d_wtiles);
   b->exec = nullptr;
   b->graph = nullptr;
   b->d_items = nullptr;
   b->d_tiles = nullptr;
+  b->d_wtiles = nullptr;
 }
 
 SU3S_EXPORT int su3s_batch_create(su3s_batch** out) {
@@ -153,7 +248,8 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   (void)stream;
 
   std::vector<BItem> hitems;
-  std::vector<BTile> by_tree[kNumBatchTrees];
+  std::vector<BTile> by_tree[kNumBatchTrees];     // plain-load tiles
+  std::vector<BWTile> staged_by_tree[kNumBatchTrees];  // 32-site tiles of staged items
   std::vector<size_t> others;  // item indices launched separately
   int64_t nsites = 0;
   for (size_t i = 0; i < b->items.size(); ++i) {
@@ -173,11 +269,18 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     it.tree = tree;
     const int32_t idx = (int32_t)hitems.size();
     hitems.push_back(it);
-    for (int mu = 0; mu < it.k.nmu; ++mu)
+    const bool staged = tma_tree_ok(c, b->items[i].dest) && it.k.nvec % 32 == 0;
+    for (int mu = 0; mu < it.k.nmu; ++mu) {
+      if (staged) {
+        for (int64_t s0 = 0; s0 < it.k.nvec; s0 += 32)
+          staged_by_tree[tree].push_back(BWTile{idx, mu, s0});
+        continue;
+      }
       for (int64_t t0 = 0; t0 < it.k.nvec; t0 += tile_sites) {
         int64_t t1 = t0 + tile_sites < it.k.nvec ? t0 + tile_sites : it.k.nvec;
         by_tree[tree].push_back(BTile{idx, mu, t0, t1});
       }
+    }
   }
   // tiles grouped by tree: group t is htiles[first[t], first[t] + count[t])
   std::vector<BTile> htiles;
@@ -187,24 +290,62 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     count[t] = (int64_t)by_tree[t].size();
     htiles.insert(htiles.end(), by_tree[t].begin(), by_tree[t].end());
   }
+  std::vector<BWTile> hwtiles;
+  int64_t wfirst[kNumBatchTrees], wcount[kNumBatchTrees];
+  for (int t = 0; t < kNumBatchTrees; ++t) {
+    wfirst[t] = (int64_t)hwtiles.size();
+    wcount[t] = (int64_t)staged_by_tree[t].size();
+    hwtiles.insert(hwtiles.end(), staged_by_tree[t].begin(), staged_by_tree[t].end());
+  }
   b->nsites = nsites;
-  b->ntiles = (int64_t)htiles.size();
+  b->ntiles = (int64_t)htiles.size() + (int64_t)hwtiles.size();
 
   cudaError_t ce;
   if (!hitems.empty()) {
     ce = cudaMalloc(&b->d_items, hitems.size() * sizeof(BItem));
-    if (ce == cudaSuccess) ce = cudaMalloc(&b->d_tiles, htiles.size() * sizeof(BTile));
+    if (ce == cudaSuccess && !htiles.empty())
+      ce = cudaMalloc(&b->d_tiles, htiles.size() * sizeof(BTile));
+    if (ce == cudaSuccess && !hwtiles.empty())
+      ce = cudaMalloc(&b->d_wtiles, hwtiles.size() * sizeof(BWTile));
     if (ce != cudaSuccess) {
       batch_release(b);
       return fail(SU3S_ENOMEM, "batch tables: %s", cudaGetErrorString(ce));
     }
     ce = cudaMemcpy(b->d_items, hitems.data(), hitems.size() * sizeof(BItem), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
+    if (ce == cudaSuccess && !htiles.empty())
       ce = cudaMemcpy(b->d_tiles, htiles.data(), htiles.size() * sizeof(BTile), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && !hwtiles.empty())
+      ce = cudaMemcpy(b->d_wtiles, hwtiles.data(), hwtiles.size() * sizeof(BWTile),
+                      cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
       batch_release(b);
       return cuda_fail(ce, "batch table upload");
     }
+  }
+
+  // staged groups: persistent grid from occupancy with the warps' tile buffers
+  int64_t wgrid[kNumBatchTrees];
+  size_t wsmem[kNumBatchTrees];
+  for (int t = 0; t < kNumBatchTrees; ++t) {
+    wgrid[t] = 1;
+    wsmem[t] = 0;
+    if (wcount[t] == 0) continue;
+    int wb = 0;
+    const void* k = batch_kernel_tma(m, t, &wb);
+    wsmem[t] = (size_t)(threads / 32) * wb;
+    int per_sm = 1;
+    ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem[t]);
+    if (ce == cudaSuccess)
+      ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, wsmem[t]);
+    if (ce != cudaSuccess) {
+      batch_release(b);
+      return cuda_fail(ce, "staged batch kernel setup");
+    }
+    if (per_sm < 1) per_sm = 1;
+    const int64_t warps = (int64_t)per_sm * sm_count() * (threads / 32);
+    int64_t blocks = (int64_t)per_sm * sm_count();
+    if (warps > wcount[t]) blocks = (wcount[t] + threads / 32 - 1) / (threads / 32);
+    wgrid[t] = blocks < 1 ? 1 : blocks;
   }
 
   // persistent grid of each group from its kernel's occupancy
@@ -228,6 +369,18 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int rc = SU3S_OK;
   if (ce == cudaSuccess) {
+    int* err = hitems.empty() ? nullptr : hitems[0].k.err;   // the library's device error word
+    for (int t = 0; t < kNumBatchTrees && !rc; ++t) {
+      if (wcount[t] == 0) continue;
+      int wb = 0;
+      const BItem* items = b->d_items;
+      const BWTile* wt = b->d_wtiles + wfirst[t];
+      int64_t n = wcount[t];
+      void* args[] = {(void*)&items, (void*)&wt, (void*)&n, (void*)&err};
+      ce = cudaLaunchKernel(batch_kernel_tma(m, t, &wb), dim3((unsigned)wgrid[t]),
+                            dim3((unsigned)threads), args, wsmem[t], cap);
+      if (ce != cudaSuccess) rc = cuda_fail(ce, "staged persistent kernel capture");
+    }
     for (int t = 0; t < kNumBatchTrees && !rc; ++t) {
       if (count[t] == 0) continue;
       const BItem* items = b->d_items;

@@ -460,10 +460,22 @@ def test_batch_matches_separate_evaluations(su3s, math):
         z = F["a"].like()
         b.add(z, F["a"] * F["b"] + F["c"] * F["d"])
         items.append((lat, host, F, z))
-    # one extra item the persistent kernel does not cover (interpreter inside the graph)
+    # one extra item the persistent kernels do not cover (interpreter inside the graph)
     _, host0, F0, _ = items[0]
     zi = F0["a"].like()
     b.add(zi, (F0["a"] + F0["b"]) * F0["c"].adj())
+    # an item that cannot be staged (4-site blocks): plain-load persistent kernel
+    lat0 = items[0][0]
+    F4 = {n: upload(su3s, lat0, host0[n], layout=1, block=4) for n in "abcd"}
+    z4 = F4["a"].like()
+    b.add(z4, F4["a"] * F4["b"] + F4["c"] * F4["d"])
+    # a second staged tree with a real factor, on Lorentz-indexed links
+    lat1, host1 = items[1][0], items[1][1]
+    v1 = synth.volume(shapes[1])
+    hl = {n: synth.su3(seed + 77, synth.FIELD[n], 4 * v1) for n in "abcd"}
+    FL = {n: upload(su3s, lat1, hl[n], nmu=4) for n in "abcd"}
+    zl = FL["a"].like()
+    b.add(zl, FL["a"] * FL["b"] * FL["c"] + 0.5 * FL["d"])
     b.build(math)
     for _ in range(2):
         b.launch()
@@ -478,6 +490,14 @@ def test_batch_matches_separate_evaluations(su3s, math):
     ref = oracle.eval_tree(("mul", ("add", ("leaf", "a"), ("leaf", "b")), ("adj", ("leaf", "c"))),
                            host0)
     assert np.abs(zi.download() - ref).max() < 4 * TOL
+    ref4 = oracle.mm(host0["a"], host0["b"]) + oracle.mm(host0["c"], host0["d"])
+    assert np.abs(z4.download() - ref4).max() < 2 * TOL
+    refl = oracle.eval_tree(E2, hl)
+    assert np.abs(zl.download() - refl).max() < 4 * TOL
+    sepl = zl.like()
+    su3s.evaluate(sepl, FL["a"] * FL["b"] * FL["c"] + 0.5 * FL["d"], math)
+    assert np.array_equal(sepl.download(), zl.download())
+    assert su3s.device_error() == 0
     sites, tiles = b.info()
     assert sites > 0 and tiles > 0
 
