@@ -54,11 +54,21 @@ MATH_DESC = {"fx": "shared-exponent fixed-point (fx)", "df32": "pair-of-FP32 (df
              "f64": "native FP64 (f64)"}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on a
-# 32^4 lattice (1,048,576 sites), from one ncu capture of the kernels as they
-# stand; scaled to the benchmark's volume in proportion to the sites (the
-# algorithmic bytes).  (row, kernel whose counters these are, bytes, algorithmic
-# bytes of that launch).  A row missing here reports traffic null.
-TRAFFIC_32 = {}
+# 32^4 lattice (1,048,576 sites; the batch row: its 64 fixed lattices), from one
+# ncu capture of the kernels as they stand (default launches); scaled to the
+# benchmark's volume in proportion to the algorithmic bytes.  (row: kernel whose
+# counters these are, bytes, algorithmic bytes of that launch).  A row missing
+# here reports traffic null.
+TRAFFIC_32 = {
+    "A2 z=a*b": ("k_eval_tma<MM,MathDF,0>", 411.3 * 1e6, 452984832),
+    "A4 z_mu=a_mu*b_mu": ("k_eval_tma<MM,MathDF,0>", 1775.9 * 1e6, 1811939328),
+    "A5 z=a*b+c*d": ("k_eval_tma<E1,MathDF,0>", 731.5 * 1e6, 754974720),
+    "A5 z=a*b*c+0.5*d": ("k_eval_tma<E2,MathDF,0>", 730.6 * 1e6, 754974720),
+    "A5 z=adj(a)*b-b*adj(a)": ("k_eval_tma<E3,MathDF,0>", 411.6 * 1e6, 452984832),
+    "A8 batch 64 lattices z=a*b+c*d": ("k_batch_tma<MathDF,E1>", 4606.2 * 1e6, 4622376960),
+    "A9 adjoint of z=a*b": ("k_adjoint_tma<MM,MathDF>", 706.0 * 1e6, 754974720),
+    "A9 adjoint of z=a*b+c*d": ("k_adjoint_tma<E1,MathDF>", 1304.2 * 1e6, 1358954496),
+}
 
 
 def traffic_bytes(row_name, nbytes):
@@ -782,7 +792,7 @@ def main():
     for mname in [m for m in MATH_NAMES if m != args.math]:
         su3s.set_default_math(MATH_IDS[mname])
         for r in (rows if not args.no_variants else []):
-            if r.dtype == "f64":
+            if r.dtype == "f64" and not r.name.startswith("A8"):   # graph fixed at build
                 _, pr, _ = time_step([r], torch, stream, 20, 2)
                 m = float(np.mean(pr[0]))
                 variants.append({"row": r.name, "math": mname, "ms": round(m, 5),

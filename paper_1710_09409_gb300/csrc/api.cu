@@ -196,7 +196,13 @@ int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* 
   const bool can_stage = e->fn[1] && tma_ok && nvec % 32 == 0;
   int variant = g.variant;
   if (variant < 0 || variant >= kNumVariants || !e->fn[variant]) variant = e->default_variant;
-  if (!can_stage) variant = 0;
+  if (!can_stage) {
+    variant = 0;
+    if (!set) {  // a staged default does not fit plain loads: take the plain defaults
+      g.threads = 0;
+      g.bps = 0;
+    }
+  }
   if (variant > 0) {
     int threads = g.threads > 0 ? g.threads : 128;
     if (variant >= 2 && threads > 128) threads = 128;  // per-leaf / ring kernels: at most 4 warps

@@ -827,13 +827,13 @@ template <class Tree, bool GRAD>
 __host__ __device__ constexpr bool ring_ok() {
   constexpr SlotSeq q = ReadSeq<Tree, GRAD>::get();
   constexpr int nobj = Tree::nleaf + (GRAD ? 1 : 0);
-  if (q.n != nobj || nobj < 3) return false;
+  bool ok = q.n == nobj && nobj >= 3;
   for (int slot = 0; slot < nobj; ++slot) {
     int c = 0;
     for (int i = 0; i < q.n; ++i) c += q.s[i] == slot;
-    if (c != 1) return false;
+    ok = ok && c == 1;
   }
-  return true;
+  return ok;
 }
 
 // Position that buffer j % K serves after position j of a tile (n objects):
@@ -1204,11 +1204,36 @@ struct Sig<Adj<X>> {
 struct DefaultGeo {
   int variant, threads, bps;
 };
-template <class Tree, class M, bool GRAD>
+// A product of two distinct leaves (either may be an adjoint).
+template <class T>
+struct IsLeafProduct {
+  static constexpr bool value = false;
+};
+template <class T, bool LEAF = T::is_leaf>
+struct SlotOf {
+  static constexpr int value = -1;
+};
+template <class T>
+struct SlotOf<T, true> {
+  static constexpr int value = T::slot;
+};
+template <class X, class Y>
+struct IsLeafProduct<Mul<X, Y>> {
+  using BX = typename Operand<X>::base;
+  using BY = typename Operand<Y>::base;
+  static constexpr bool value =
+      BX::is_leaf && BY::is_leaf && SlotOf<BX>::value != SlotOf<BY>::value;
+};
+
+template <class Tree, class M, int PREC, bool GRAD>
 constexpr DefaultGeo default_geometry() {
   // With one tensor copy per object, whole-tile staging is the fastest data
-  // movement for every FP64 tree measured, in both FP64-accurate arithmetics
+  // movement for every FP64 tree measured, in both FP64-accurate arithmetics.
+  // Forward products of two leaves run best in small blocks, about 8 warps
+  // per SM (16 for matrix times vector); the rest with the most that fit.
   if constexpr (M::kScaled) return DefaultGeo{1, 128, 0};
+  else if constexpr (!GRAD && PREC == P_F64 && IsLeafProduct<Tree>::value)
+    return Tree::kind == KV ? DefaultGeo{1, 64, 8} : DefaultGeo{1, 64, 4};
   else return DefaultGeo{1, 256, 0};
 }
 
@@ -1243,7 +1268,7 @@ void reg_eval(int math) {
       v.kernel[3] = (const void*)&k_eval_ring<Tree, M, PREC>;
       v.warp_bytes[3] = RingLayout<Tree, PREC, false>::STRIDE;
     }
-    constexpr DefaultGeo g = default_geometry<Tree, M, false>();
+    constexpr DefaultGeo g = default_geometry<Tree, M, PREC, false>();
     v.default_variant = g.variant;
     v.default_threads = g.threads;
     v.default_bps = g.bps;
@@ -1267,7 +1292,7 @@ void reg_adjoint(int math) {
     v.kernel[3] = (const void*)&k_adjoint_ring<Tree, M>;
     v.warp_bytes[3] = RingLayout<Tree, P_F64, true>::STRIDE;
   }
-  constexpr DefaultGeo g = default_geometry<Tree, M, true>();
+  constexpr DefaultGeo g = default_geometry<Tree, M, P_F64, true>();
   v.default_variant = g.variant;
   v.default_threads = g.threads;
   v.default_bps = g.bps;

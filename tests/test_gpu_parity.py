@@ -601,7 +601,7 @@ def test_launch_geometry_does_not_change_results(su3s):
         th, bps, var, ms = su3s.tune(z, e, math)
         su3s.evaluate(z, e, math)
         assert np.array_equal(z.download(), ref) and th in (64, 128, 256) and ms > 0
-        assert var in (0, 1, 2)
+        assert var in (0, 1, 2, 3)
         outs.append(ref)
 
 
