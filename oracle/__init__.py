@@ -15,6 +15,9 @@ for the definitions):
   c12_expand      third row of an SU(3) matrix rebuilt from rows 0 and 1
   redot           sum_x Re tr(X^dagger Y)
   reunitarize     projection to SU(3): Gram-Schmidt over rows, det phase removed
+  cshift          Sec. 7 (Cshift): circular shift along one lattice direction
+  hop             Sec. 7 (Dslash): colour part of the nearest-neighbour
+                  hopping term, sum_mu U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu)
 
 Parity status: every function here is pinned by the CPU tests in
 tests/test_oracle.py (brute force against numpy/torch, closed forms,
@@ -71,6 +74,10 @@ def _bind(lib):
     lib.oracle_redot.argtypes = [P, P, I64]
     lib.oracle_redot.restype = ctypes.c_double
     lib.oracle_reunitarize.argtypes = [P, P, I64]
+    lib.oracle_cshift.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.oracle_cshift.restype = None
+    lib.oracle_hop.argtypes = [P, P, P, P, ctypes.c_int]
+    lib.oracle_hop.restype = None
     return lib
 
 
@@ -238,4 +245,35 @@ def reunitarize(x):
     x = _c(x)
     out = np.empty_like(x)
     _load().oracle_reunitarize(x.ctypes.data, out.ctypes.data, x.shape[0])
+    return out
+
+
+def _dims(dims):
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    assert all(x >= 1 for x in dims)
+    return d
+
+
+def cshift(x, dims, dim, shift):
+    """dst(s) = x(s + shift * e_dim), periodic (Sec. 7's Cshift).  x: canonical
+    field array whose first axis runs over sites (all links and components of
+    a site follow)."""
+    x = _c(x)
+    v = int(np.prod(dims))
+    assert x.shape[0] == v and 0 <= dim < 4
+    out = np.empty_like(x)
+    _load().oracle_cshift(x.ctypes.data, out.ctypes.data, _dims(dims), x.size // v, dim, shift)
+    return out
+
+
+def hop(u, x, dims):
+    """out(s) = sum_mu U_mu(s) x(s+mu) + U_mu(s-mu)^dagger x(s-mu): the colour part
+    of the Dslash hopping term (Sec. 7).  u: (V*4, 3, 3, 2) links; x: (V, 3, 3, 2)
+    matrices or (V, 3, 2) vectors."""
+    u, x = _c(u), _c(x)
+    v = int(np.prod(dims))
+    assert u.shape == (4 * v, 3, 3, 2) and x.shape[0] == v
+    kind = {(3, 3, 2): 0, (3, 2): 1}[x.shape[1:]]
+    out = np.empty_like(x)
+    _load().oracle_hop(u.ctypes.data, x.ctypes.data, out.ctypes.data, _dims(dims), kind)
     return out

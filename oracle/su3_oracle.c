@@ -33,6 +33,16 @@
  *   oracle_redot   sum over all reals of x*y (= sum_x Re tr(X^dagger Y)).
  *   oracle_reunitarize  Gram-Schmidt over rows and removal of the determinant
  *                  phase (principal cube root), in FP64.
+ *   oracle_cshift  circular shift of a field along one lattice direction,
+ *                  dst(x) = src(x + shift * e_dim) with periodic wrap (the
+ *                  Cshift operation the paper names as the next step beside
+ *                  its Dslash port, Sec. 7).
+ *   oracle_hop     the colour part of the Wilson Dslash operator, the
+ *                  nearest-neighbour hopping term of Sec. 7:
+ *                  out(x) = sum_mu [ U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu) ],
+ *                  v a colour vector or a colour matrix field, U the 4 links.
+ *                  Site order: s = x + Lx*(y + Ly*(z + Lz*t)); directions
+ *                  0..3 = x, y, z, t.
  */
 #include <math.h>
 #include <stdint.h>
@@ -406,6 +416,56 @@ void oracle_reunitarize(const double* in, double* out, int64_t n) {
         for (int q = 0; q < 9; ++q) {
             o[2 * q] = c * r[2 * q] - s * r[2 * q + 1];
             o[2 * q + 1] = c * r[2 * q + 1] + s * r[2 * q];
+        }
+    }
+}
+
+/* ---------- neighbours: Cshift and the hopping term ---------- */
+
+/* site index of (x,y,z,t) + shift * e_dim, periodic */
+static int64_t shifted_site(int64_t s, const int* L, int dim, int shift) {
+    int64_t c[4];
+    int64_t r = s;
+    for (int d = 0; d < 4; ++d) {
+        c[d] = r % L[d];
+        r /= L[d];
+    }
+    int64_t m = ((c[dim] + shift) % L[dim] + L[dim]) % L[dim];
+    c[dim] = m;
+    return c[0] + (int64_t)L[0] * (c[1] + (int64_t)L[1] * (c[2] + (int64_t)L[2] * c[3]));
+}
+
+/* dst(x) = src(x + shift e_dim); `width` doubles per site (all links and
+ * components of the site). */
+void oracle_cshift(const double* src, double* dst, const int* L, int width, int dim, int shift) {
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    for (int64_t s = 0; s < V; ++s) {
+        const int64_t n = shifted_site(s, L, dim, shift);
+        memcpy(dst + width * s, src + width * n, sizeof(double) * (size_t)width);
+    }
+}
+
+/* out(x) = sum_mu U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu); U: 4 links per
+ * site (double[V][4][3][3][2]); v, out: matrix (kind 0) or vector (kind 1). */
+void oracle_hop(const double* U, const double* v, double* out, const int* L, int kind) {
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    const int w = width_of(kind);
+    double t[18], a[18];
+    for (int64_t s = 0; s < V; ++s) {
+        double* o = out + w * s;
+        for (int r = 0; r < w; ++r) o[r] = 0.0;
+        for (int mu = 0; mu < 4; ++mu) {
+            const int64_t fw = shifted_site(s, L, mu, +1);
+            const int64_t bw = shifted_site(s, L, mu, -1);
+            /* forward: U_mu(x) v(x+mu) */
+            if (kind == OR_MATRIX) mat_mul(U + 18 * (4 * s + mu), v + w * fw, t);
+            else mat_vec(U + 18 * (4 * s + mu), v + w * fw, t);
+            for (int r = 0; r < w; ++r) o[r] += t[r];
+            /* backward: U_mu(x-mu)^dagger v(x-mu) */
+            mat_adj(U + 18 * (4 * bw + mu), a);
+            if (kind == OR_MATRIX) mat_mul(a, v + w * bw, t);
+            else mat_vec(a, v + w * bw, t);
+            for (int r = 0; r < w; ++r) o[r] += t[r];
         }
     }
 }

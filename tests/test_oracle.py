@@ -399,3 +399,108 @@ def test_generator_gaussian_moments():
     assert abs(g.mean()) < 0.01 and abs(g.std() - 1.0) < 0.01
     s = synth.uniform_real(5, 6, 100000)
     assert s.min() > -1.0 and s.max() < 1.0 and abs(s.mean()) < 0.01
+
+
+# ------------------------------------------------ neighbours (Sec. 7)
+STENCIL_DIMS = [(3, 2, 5, 4), (1, 3, 1, 2), (4, 4, 4, 4)]
+
+
+def lattice_axis(dim):
+    """Axis of a site-major array reshaped to (Lt, Lz, Ly, Lx, ...) for direction dim."""
+    return 3 - dim
+
+
+def as_grid(a, dims):
+    return a.reshape(tuple(reversed(dims)) + a.shape[1:])
+
+
+@pytest.mark.parametrize("dims", STENCIL_DIMS)
+def test_cshift_matches_numpy_roll(dims):
+    v = synth.volume(dims)
+    links = synth.su3(SEED, 0, 4 * v).reshape(v, 4, 3, 3, 2)   # 4 links per site
+    for dim in range(4):
+        for shift in (-3, -1, 1, 2, 5):
+            got = oracle.cshift(links, dims, dim, shift)
+            # dst(x) = src(x + shift e_dim)  <=>  roll by -shift along that axis
+            ref = np.roll(as_grid(links, dims), -shift, axis=lattice_axis(dim)).reshape(links.shape)
+            assert np.array_equal(got, ref)
+
+
+def test_cshift_inverse_and_period():
+    dims = (3, 2, 5, 4)
+    x = synth.gauss_vector(SEED, 4, synth.volume(dims))
+    for dim in range(4):
+        assert np.array_equal(oracle.cshift(oracle.cshift(x, dims, dim, 1), dims, dim, -1), x)
+        assert np.array_equal(oracle.cshift(x, dims, dim, dims[dim]), x)
+        y = x
+        for _ in range(dims[dim]):
+            y = oracle.cshift(y, dims, dim, 1)
+        assert np.array_equal(y, x)
+
+
+def hop_numpy(u, x, dims):
+    """Independent restatement with numpy rolls and einsum."""
+    v = synth.volume(dims)
+    U = as_grid(cplx(u).reshape(v, 4, 3, 3), dims)
+    X = as_grid(cplx(x), dims)
+    out = np.zeros_like(X)
+    mat = X.ndim == 6
+    for mu in range(4):
+        ax = lattice_axis(mu)
+        Um = U[..., mu, :, :]
+        fwd = np.roll(X, -1, axis=ax)                    # x(s + mu)
+        bwd = np.roll(X, 1, axis=ax)                     # x(s - mu)
+        Ub = np.conj(np.swapaxes(np.roll(Um, 1, axis=ax), -1, -2))   # U_mu(s - mu)^dagger
+        if mat:
+            out += np.einsum("...ij,...jk->...ik", Um, fwd) + np.einsum("...ij,...jk->...ik", Ub, bwd)
+        else:
+            out += np.einsum("...ij,...j->...i", Um, fwd) + np.einsum("...ij,...j->...i", Ub, bwd)
+    return out.reshape((v,) + out.shape[4:])
+
+
+@pytest.mark.parametrize("dims", STENCIL_DIMS)
+@pytest.mark.parametrize("kind", ["vector", "matrix"])
+def test_hop_matches_numpy(dims, kind):
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    x = synth.gauss_vector(SEED, 4, v) if kind == "vector" else synth.gauss_matrix(SEED, 5, v)
+    got = cplx(oracle.hop(u, x, dims))
+    assert np.abs(got - hop_numpy(u, x, dims)).max() < 1e-13
+
+
+def test_hop_unit_links_constant_field():
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = np.zeros((4 * v, 3, 3, 2))
+    u[:, [0, 1, 2], [0, 1, 2], 0] = 1.0
+    # dyadic components with few bits: every partial sum is exact
+    x = np.broadcast_to(np.round(16 * synth.gauss_vector(SEED, 4, 1)) / 16, (v, 3, 2)).copy()
+    assert np.array_equal(oracle.hop(u, x, dims), 8.0 * x)
+
+
+def test_hop_is_hermitian():
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    a, b = synth.gauss_vector(SEED, 4, v), synth.gauss_vector(SEED + 1, 4, v)
+    lhs = np.vdot(cplx(a), cplx(oracle.hop(u, b, dims)))
+    rhs = np.vdot(cplx(oracle.hop(u, a, dims)), cplx(b))
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def test_hop_gauge_covariance():
+    """U'_mu(x) = g(x) U_mu(x) g(x+mu)^dagger, v'(x) = g(x) v(x) give hop'(x) = g(x) hop(x)."""
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    x = synth.gauss_matrix(SEED, 5, v)
+    g = synth.su3(SEED + 9, 2, v)
+    G, U = cplx(g), cplx(u).reshape(v, 4, 3, 3)
+    Up = np.empty_like(U)
+    for mu in range(4):
+        gn = cplx(oracle.cshift(g, dims, mu, 1))          # g(x + mu)
+        Up[:, mu] = G @ U[:, mu] @ np.conj(np.swapaxes(gn, -1, -2))
+    xp = G @ cplx(x)
+    up = np.stack([Up.real, Up.imag], -1).reshape(4 * v, 3, 3, 2)
+    hp = oracle.hop(up, np.stack([xp.real, xp.imag], -1), dims)
+    assert np.abs(cplx(hp) - G @ cplx(oracle.hop(u, x, dims))).max() < 1e-13

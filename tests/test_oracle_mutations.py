@@ -72,6 +72,24 @@ def pin_reunitarize_det():
             and np.abs(np.linalg.det(u) - 1).max() < 1e-14)
 
 
+def pin_cshift_roll():
+    dims = (3, 2, 5, 4)
+    x = synth.gauss_vector(SEED, 4, synth.volume(dims))
+    g = x.reshape(4, 5, 2, 3, 3, 2)
+    return all(np.array_equal(oracle.cshift(x, dims, d, 1),
+                              np.roll(g, -1, axis=3 - d).reshape(x.shape)) for d in range(4))
+
+
+def pin_hop_hermitian():
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    a, b = synth.gauss_vector(SEED, 4, v), synth.gauss_vector(SEED + 1, 4, v)
+    lhs = np.vdot(cplx(a), cplx(oracle.hop(u, b, dims)))
+    rhs = np.vdot(cplx(oracle.hop(u, a, dims)), cplx(b))
+    return abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
 MUTATIONS = [
     ("mm sign", "re -= xi * yi;", "re += xi * yi;", pin_mm_brute_force),
     ("mm transposed operand", "double yr = y[2 * (3 * j + k)], yi = y[2 * (3 * j + k) + 1];",
@@ -93,6 +111,12 @@ MUTATIONS = [
      pin_round_bf16_ties),
     ("reunitarize keeps det phase", "double phi = atan2(di, dr);", "double phi = 0.0 * atan2(di, dr);",
      pin_reunitarize_det),
+    ("cshift wrong direction", "int64_t m = ((c[dim] + shift) % L[dim] + L[dim]) % L[dim];",
+     "int64_t m = ((c[dim] - shift) % L[dim] + L[dim]) % L[dim];", pin_cshift_roll),
+    ("hop backward link not daggered", "mat_adj(U + 18 * (4 * bw + mu), a);",
+     "memcpy(a, U + 18 * (4 * bw + mu), sizeof a);", pin_hop_hermitian),
+    ("hop backward link at the site", "mat_adj(U + 18 * (4 * bw + mu), a);",
+     "mat_adj(U + 18 * (4 * s + mu), a);", pin_hop_hermitian),
 ]
 
 
