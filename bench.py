@@ -609,6 +609,37 @@ def run_studies(su3s, synth, torch, stream, which):
             del F, a, b, c, d, z, exprs
             torch.cuda.empty_cache()
 
+    if "stencil" in which:
+        # nearest-neighbour operations (Sec. 7): the hopping term and the Cshift;
+        # algorithmic bytes: every input object once, the output once
+        for dims in ((32, 32, 32, 32), (48, 48, 48, 48)):
+            v = synth.volume(dims)
+            lat = su3s.Lattice(dims)
+            U = fld(lat, MAT, 4, F64, synth.su3(SEED + 6, 0, 4 * v))
+            for kind, name, bsite in ((su3s.VECTOR, "vector", 576 + 48 + 48),
+                                      (MAT, "matrix", 576 + 144 + 144)):
+                x = (synth.gauss_vector(SEED + 6, 4, v) if kind == su3s.VECTOR
+                     else synth.su3(SEED + 6, 1, v))
+                X = fld(lat, kind, 1, F64, x)
+                Z = X.like()
+                for mname in MATH_NAMES:
+                    ms = _time_ms(torch, stream,
+                                  lambda: su3s.hop(Z, U, X, MATH_IDS[mname], stream))
+                    out.append({"study": "stencil", "op": "hop " + name, "lattice": list(dims),
+                                "math": mname, "ms": round(ms, 5), "B_per_site": bsite,
+                                "GB_s": round(bsite * v / ms / 1e6, 1),
+                                "Gsites_s": round(v / ms / 1e6, 3)})
+                del X, Z
+            A = fld(lat, MAT, 1, F64, synth.su3(SEED + 6, 2, v))
+            B = A.like()
+            for dim in (0, 3):
+                ms = _time_ms(torch, stream, lambda: su3s.cshift(B, A, dim, 1, stream))
+                out.append({"study": "stencil", "op": "cshift matrix dim %d" % dim,
+                            "lattice": list(dims), "ms": round(ms, 5), "B_per_site": 288,
+                            "GB_s": round(288 * v / ms / 1e6, 1)})
+            del U, A, B
+            torch.cuda.empty_cache()
+
     if "batch" in which:
         picks = (synth.uniform_real(SEED + 3, 40, 64) + 1.0) / 2.0 * len(BATCH_SHAPES)
         batch = su3s.Batch()
@@ -680,7 +711,7 @@ def main():
     ap.add_argument("--dims", default="48,48,48,48", help="lattice extents (default 48^4)")
     ap.add_argument("--study", default="",
                     help="comma list of studies to run instead of the step: volume, fused, "
-                         "precision, error, batch, layout (one JSON line each)")
+                         "precision, error, batch, layout, stencil (one JSON line each)")
     ap.add_argument("--math", default="df32", choices=["fx", "df32", "f64"],
                     help="arithmetic of the FP64-storage rows in the step (the others are "
                          "timed beside it)")

@@ -363,6 +363,29 @@ int su3s_field_redot(const su3s_field* x, const su3s_field* y, double* dev_out, 
  * Pad sites are not touched. */
 int su3s_reunitarize(su3s_field* dst, const su3s_field* src, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Nearest-neighbour operations (arXiv:1710.09409 Sec. 7: the Dslash operator
+ * and the Cshift operations outside the expression templates are the paper's
+ * next step).  Sites are s = x + Lx (y + Ly (z + Lz t)); directions 0..3 are
+ * x, y, z, t; every direction is periodic.
+ * ---------------------------------------------------------------------- */
+
+/* dst(x) = src(x + shift * e_dim) at every site, link and component: a copy
+ * of the stored objects in their storage format (any kind and precision,
+ * bit exact).  dst and src have the same kind, shape, precision and layout
+ * and do not overlap (EINVAL).  dim in 0..3 (EINVAL otherwise); any shift,
+ * taken modulo the extent.  Pad sites are not touched. */
+int su3s_cshift(su3s_field* dst, const su3s_field* src, int dim, int shift, void* stream);
+
+/* dst(x) = sum_mu [ U_mu(x) v(x + mu) + U_mu(x - mu)^dagger v(x - mu) ]: the
+ * colour part of the Wilson Dslash hopping term.  U: matrix field with 4 links
+ * per site; v, dst: matrix or colour-vector fields with one object per site,
+ * of the same kind; all FP64 storage on one lattice (any layouts).  Each of
+ * the 8 products is accumulated on its own and the products are added in the
+ * arithmetic `math` (as for su3s_eval_math).  dst overlapping U or v: EINVAL.
+ * Pad sites are not touched. */
+int su3s_hop(su3s_field* dst, const su3s_field* U, const su3s_field* v, int math, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

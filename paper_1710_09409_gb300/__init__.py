@@ -100,6 +100,8 @@ def load(build_if_missing=False):
                                ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)], I),
         "su3s_field_redot": ([P, P, P, P], I),
         "su3s_reunitarize": ([P, P, P], I),
+        "su3s_cshift": ([P, P, I, I, P], I),
+        "su3s_hop": ([P, P, P, I, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -433,6 +435,19 @@ def redot(x, y, out=None, stream=None):
 def reunitarize(dst, src, stream=None):
     """dst = projection of src to SU(3) at every site."""
     _check(_lib.su3s_reunitarize(dst._h, src._h, _stream(stream)))
+    return dst
+
+
+def cshift(dst, src, dim, shift, stream=None):
+    """dst(x) = src(x + shift e_dim), periodic (directions 0..3 = x, y, z, t)."""
+    _check(_lib.su3s_cshift(dst._h, src._h, int(dim), int(shift), _stream(stream)))
+    return dst
+
+
+def hop(dst, links, v, math=MATH_DEFAULT, stream=None):
+    """dst(x) = sum_mu U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu), the colour
+    part of the Dslash hopping term; `links` holds the 4 links of every site."""
+    _check(_lib.su3s_hop(dst._h, links._h, v._h, math, _stream(stream)))
     return dst
 
 

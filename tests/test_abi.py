@@ -264,3 +264,37 @@ def test_pipeline_modes(L):
     assert L.su3s_set_pipeline(4) == 1
     assert L.su3s_set_pipeline(-2) == 1
     assert L.su3s_set_pipeline(-1) == 0
+
+
+def _wrap(L, lat, kind, nmu, prec, addr):
+    n = ctypes.c_size_t()
+    assert L.su3s_field_bytes(lat, kind, nmu, prec, su3s.SOA, 0, ctypes.byref(n)) == 0
+    h = ctypes.c_void_p()
+    assert L.su3s_field_wrap(lat, kind, nmu, prec, su3s.SOA, 0, addr, n.value, ctypes.byref(h)) == 0
+    return h
+
+
+def test_neighbour_operation_validation(L):
+    """Argument checks of su3s_cshift and su3s_hop (nothing reaches the GPU)."""
+    rc, lat = _lat(L, (2, 2, 2, 2))
+    rc2, other = _lat(L, (2, 2, 2, 3))
+    gap = 1 << 24
+    m1 = _wrap(L, lat, su3s.MATRIX, 1, su3s.F64, FAKE)
+    m2 = _wrap(L, lat, su3s.MATRIX, 1, su3s.F64, FAKE + gap)
+    v1 = _wrap(L, lat, su3s.VECTOR, 1, su3s.F64, FAKE + 2 * gap)
+    v2 = _wrap(L, lat, su3s.VECTOR, 1, su3s.F64, FAKE + 3 * gap)
+    u4 = _wrap(L, lat, su3s.MATRIX, 4, su3s.F64, FAKE + 4 * gap)
+    f32 = _wrap(L, lat, su3s.MATRIX, 1, su3s.F32, FAKE + 5 * gap)
+    mo = _wrap(L, other, su3s.MATRIX, 1, su3s.F64, FAKE + 6 * gap)
+    assert L.su3s_cshift(m1, m2, 4, 1, None) == 1                 # direction
+    assert L.su3s_cshift(m1, m2, -1, 1, None) == 1
+    assert L.su3s_cshift(m1, m1, 0, 1, None) == 1                 # overlap
+    assert L.su3s_cshift(m1, v1, 0, 1, None) == 2                 # kind
+    assert L.su3s_cshift(m1, f32, 0, 1, None) == 3                # precision
+    assert L.su3s_cshift(m1, mo, 0, 1, None) == 3                 # lattice
+    assert L.su3s_hop(v2, m2, v1, 0, None) == 2                   # links need 4 per site
+    assert L.su3s_hop(m1, u4, v1, 0, None) == 2                   # destination kind
+    assert L.su3s_hop(v1, u4, v1, 0, None) == 1                   # overlap
+    assert L.su3s_hop(f32, u4, m2, 0, None) == 6                  # FP64 only
+    assert L.su3s_hop(mo, u4, m2, 0, None) == 3                   # lattice
+    assert L.su3s_hop(v2, u4, v1, 9, None) == 1                   # arithmetic
