@@ -271,6 +271,11 @@ cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
       }
       uint64_t thr = ~0ull;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      // An allocation must never make its stream wait for another stream's
+      // work (uploads and downloads on different streams overlap): no reuse
+      // through dependencies the pool would insert itself.
+      int no = 0;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
   }
   return cudaMallocFromPoolAsync(p, bytes, pool, st);

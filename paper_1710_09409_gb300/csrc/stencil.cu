@@ -94,31 +94,52 @@ __device__ __forceinline__ void load_nc(const FieldDesc& f, int64_t s, int mu, t
   M::template normalize_obj<W>(out);
 }
 
+// Site of s + shift e_mu for a runtime direction (the geometry is selected,
+// not indexed, so it stays in registers).
+__device__ __forceinline__ int64_t shift_site_rt(const LatGeo& g, int64_t s, int mu, int shift) {
+  const uint32_t st = (uint32_t)(mu == 0 ? g.stride[0] : mu == 1 ? g.stride[1] : mu == 2 ? g.stride[2] : g.stride[3]);
+  const uint32_t L = (uint32_t)(mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3]);
+  const int32_t c = (int32_t)(((uint32_t)s / st) % L);
+  int32_t c2 = c + shift;
+  c2 = c2 >= (int32_t)L ? c2 - (int32_t)L : (c2 < 0 ? c2 + (int32_t)L : c2);
+  return s + (int64_t)(c2 - c) * st;
+}
+
+// One thread per site; the grid is one wave, so the sites in flight (and the
+// backward links and neighbours they share) fit the L2 cache; the loop over
+// directions is not unrolled, which keeps the code a quarter as large.
 template <class M, int KIND>
 __global__ void __launch_bounds__(128) k_hop(FieldDesc dst, FieldDesc U, FieldDesc v, LatGeo g) {
   constexpr int W = KIND == KM ? 18 : 6;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.V;
        s += (int64_t)gridDim.x * blockDim.x) {
     typename M::A acc[W];
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
+    {
+      // mu = 0 forward term opens the accumulators
       typename M::R u[18], x[W];
-      // forward: U_mu(x) v(x + mu)
-      load_nc<M, 18>(U, s, mu, u);
-      load_nc<M, W>(v, shift_site(g, s, mu, 1), 0, x);
-      if (mu == 0) {
-        if constexpr (KIND == KM) mm_acc<M, true, 1, false, false>(acc, u, x);
-        else mv_acc<M, true, 1, false>(acc, u, x);
-      } else {
+      load_nc<M, 18>(U, s, 0, u);
+      load_nc<M, W>(v, shift_site_rt(g, s, 0, 1), 0, x);
+      if constexpr (KIND == KM) mm_acc<M, true, 1, false, false>(acc, u, x);
+      else mv_acc<M, true, 1, false>(acc, u, x);
+    }
+#pragma unroll 1
+    for (int t = 1; t < 8; ++t) {
+      // t = 2 mu: forward U_mu(x) v(x + mu); t = 2 mu + 1: backward
+      // U_mu(x - mu)^dagger v(x - mu), the link read transposed
+      const int mu = t >> 1;
+      typename M::R u[18], x[W];
+      if ((t & 1) == 0) {
+        load_nc<M, 18>(U, s, mu, u);
+        load_nc<M, W>(v, shift_site_rt(g, s, mu, 1), 0, x);
         if constexpr (KIND == KM) mm_combine<M, 1, false, false>(acc, u, x);
         else mv_combine<M, 1, false>(acc, u, x);
+      } else {
+        const int64_t bw = shift_site_rt(g, s, mu, -1);
+        load_nc<M, 18>(U, bw, mu, u);
+        load_nc<M, W>(v, bw, 0, x);
+        if constexpr (KIND == KM) mm_combine<M, 1, true, false>(acc, u, x);
+        else mv_combine<M, 1, true>(acc, u, x);
       }
-      // backward: U_mu(x - mu)^dagger v(x - mu), the link read transposed
-      const int64_t bw = shift_site(g, s, mu, -1);
-      load_nc<M, 18>(U, bw, mu, u);
-      load_nc<M, W>(v, bw, 0, x);
-      if constexpr (KIND == KM) mm_combine<M, 1, true, false>(acc, u, x);
-      else mv_combine<M, 1, true>(acc, u, x);
     }
     typename M::A out[1][W];
 #pragma unroll
@@ -158,7 +179,11 @@ template <class M, int KIND>
 static cudaError_t launch_hop(const su3s_field* dest, const su3s_field* U, const su3s_field* v,
                               cudaStream_t st) {
   const LatGeo g = lat_geo(v);
-  const dim3 grid = grid_for(k_hop<M, KIND>, 128, g.V);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop<M, KIND>, 128, 0);
+  int64_t nb = (int64_t)(per_sm > 0 ? per_sm : 1) * sm_count();   // one wave
+  const int64_t need = (g.V + 127) / 128;
+  const dim3 grid((unsigned)(nb < need ? nb : need));
   k_hop<M, KIND><<<grid, 128, 0, st>>>(dest->desc, U->desc, v->desc, g);
   return cudaGetLastError();
 }
