@@ -265,7 +265,9 @@ int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int th
  *   -1  the library's choice per kernel (default);
  *    0  plain 16-byte vector loads;
  *    1  TMA-staged tiles: each warp stages its next 32-site tile of every leaf
- *       with bulk copies into shared memory while it computes the current one;
+ *       into shared memory while it computes the current one, one 2-D tensor
+ *       copy per matrix or vector object (the field's tensor map, made when
+ *       the field is wrapped);
  *    2  TMA-staged per leaf: each leaf has its own buffer and barrier, is read
  *       when first needed and refilled after its last use;
  *    3  TMA-staged through a ring of three buffers per warp, for trees that

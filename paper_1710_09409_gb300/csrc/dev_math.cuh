@@ -72,10 +72,6 @@ __device__ __forceinline__ df df_split_bits(uint32_t lo32, uint32_t hi32) {
   return df{xh, __fmul_rn(m, pw)};
 }
 
-__device__ __forceinline__ df df_split(double x) {
-  return df_split_bits((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
-}
-
 // (S, lo) with |lo| << |S| (not necessarily normalised) -> FP64.
 __device__ __forceinline__ double df_to_double(float S, float lo) {
   float s = __fadd_rz(S, lo);          // toward zero: the remainder shares s's sign
@@ -103,9 +99,7 @@ __device__ __forceinline__ df df_norm(float S, float lo) {
 struct MathF64 {
   using R = double;   // one real component
   using A = double;   // accumulator
-  static constexpr bool kNative64 = true;
   static constexpr bool kScaled = false;  // every term shares one scale
-  __device__ static __forceinline__ R from_f64(double x) { return x; }
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return __hiloint2double((int)hi, (int)lo);
   }
@@ -144,9 +138,7 @@ struct DAcc {
 struct MathDF {
   using R = df;
   using A = DAcc;
-  static constexpr bool kNative64 = false;
   static constexpr bool kScaled = false;
-  __device__ static __forceinline__ R from_f64(double x) { return df_split(x); }
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return df_split_bits(lo, hi);
   }
@@ -259,7 +251,6 @@ __device__ __forceinline__ long long fx_total(const FAcc& a) {
 struct MathFX {
   using R = fxr;
   using A = FAcc;
-  static constexpr bool kNative64 = false;
   static constexpr bool kScaled = true;  // terms of different objects differ in scale
 
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
@@ -382,7 +373,6 @@ struct MathFX {
 struct MathF32 {
   using R = float;
   using A = float;
-  static constexpr bool kNative64 = false;
   static constexpr bool kScaled = false;
   __device__ static __forceinline__ R finish(const A& a) { return a; }
   __device__ static __forceinline__ A to_acc(const R& x) { return x; }
