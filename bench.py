@@ -226,12 +226,14 @@ def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True)
     shared_out = {}
 
     def out_pin(f):
-        # outputs of equal size share one pinned buffer (downloads are stream-ordered)
+        # outputs of equal size share a pair of pinned buffers, one per download
+        # stream (downloads on one stream are ordered, so they never overlap)
         n = int(np.prod(f.canonical_shape))
         if not with_host:
             return None
         if n not in shared_out:
-            shared_out[n] = torch.empty(n, dtype=torch.float64).pin_memory()
+            shared_out[n] = tuple(torch.empty(n, dtype=torch.float64).pin_memory()
+                                  for _ in range(2))
         return shared_out[n]
 
     def mk(name, bps, dest, expr, ins, dtype="f64"):
@@ -368,12 +370,15 @@ def time_step(rows, torch, stream, steps, warmup, per_row_events=True):
 
 def time_e2e(rows, torch, stream, steps):
     """The step through the C ABI from pinned host buffers.  Every distinct
-    input field is uploaded (H2D copy + pack kernel) once per step on an upload
-    stream, each row runs on the compute stream as soon as its inputs are in,
-    and its outputs are unpacked and copied back on a download stream; events
-    order the three, so host->device copies, kernels and device->host copies
-    of different rows overlap.  Returns (ms per step, H2D bytes, D2H bytes)."""
-    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    input field is uploaded (H2D copy + pack kernel) once per step on one of
+    two upload streams, each row runs on the compute stream as soon as its
+    inputs are in, and its outputs are unpacked and copied back on one of two
+    download streams; events order them, so host->device copies, kernels and
+    device->host copies of different rows overlap, and a copy does not wait for
+    the previous field's pack or unpack kernel.  Returns (ms per step, H2D
+    bytes, D2H bytes)."""
+    ups = [torch.cuda.Stream(), torch.cuda.Stream()]
+    downs = [torch.cuda.Stream(), torch.cuda.Stream()]
     comp = stream
     fields, order = {}, []
     for r in rows:
@@ -385,14 +390,16 @@ def time_e2e(rows, torch, stream, steps):
 
     def one():
         ready = {}
-        for fid in order:
+        for k, fid in enumerate(order):
             f, h = fields[fid]
+            up = ups[k % 2]
             if fid in last_use:                 # previous step's readers are done with f
                 up.wait_event(last_use[fid])
             f.upload(h, up)
             ev = torch.cuda.Event()
             ev.record(up)
             ready[fid] = ev
+        nout = 0
         for r in rows:
             for f, _ in r.inputs:
                 comp.wait_event(ready[id(f)])
@@ -401,26 +408,29 @@ def time_e2e(rows, torch, stream, steps):
             done.record(comp)
             for f, _ in r.inputs:
                 last_use[id(f)] = done
-            down.wait_event(done)
             for f, h in r.outputs:
-                f.download(out=h, stream=down)
-        fin = torch.cuda.Event()
-        fin.record(down)
-        comp.wait_event(fin)                    # outputs reused next step only after download
+                down, buf = downs[nout % 2], h[nout % 2]
+                nout += 1
+                down.wait_event(done)
+                f.download(out=buf, stream=down)
+        for down in downs:                      # outputs reused next step only after download
+            fin = torch.cuda.Event()
+            fin.record(down)
+            comp.wait_event(fin)
 
     one()
     torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(comp)
-    up.wait_stream(comp)
-    down.wait_stream(comp)
+    for st_ in ups + downs:
+        st_.wait_stream(comp)
     for _ in range(steps):
         one()
     end.record(comp)
     end.synchronize()
     torch.cuda.synchronize()
     h2d = sum(fields[fid][1].numel() * 8 for fid in order)
-    d2h = sum(h.numel() * 8 for r in rows for _, h in r.outputs)
+    d2h = sum(h[0].numel() * 8 for r in rows for _, h in r.outputs)
     return start.elapsed_time(end) / steps, h2d, d2h
 
 
