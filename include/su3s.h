@@ -302,7 +302,9 @@ int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream, int*
 
 int su3s_batch_create(su3s_batch** out);
 /* Queue dest = e.  The batch keeps references to the expression; fields must
- * outlive the batch.  Items must use FP64 storage. */
+ * outlive the batch.  Items must use FP64 storage.  Items run concurrently and
+ * in no defined order: an item's dest may be one of its own leaves, but must
+ * not overlap another item's dest or leaves (su3s_batch_build returns EINVAL). */
 int su3s_batch_add(su3s_batch* b, su3s_field* dest, const su3s_expr* e);
 /* Freeze the batch: build the tile list (tile_sites sites per tile; 0 = 2 x
  * threads) and item table in library-owned device memory, choose the

@@ -196,6 +196,12 @@ struct su3s_batch {
   cudaGraphExec_t exec = nullptr;
 };
 
+static bool overlaps(const su3s_field* a, const su3s_field* b) {
+  const char* pa = (const char*)a->ptr;
+  const char* pb = (const char*)b->ptr;
+  return pa < pb + b->bytes && pb < pa + a->bytes;
+}
+
 static void batch_release(su3s_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -246,6 +252,20 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     return fail(SU3S_EINVAL, "bad arithmetic %d", math);
   int m = resolve_math(SU3S_F64, math);
   (void)stream;
+  // items run concurrently: no item may write memory another item reads or writes
+  for (size_t i = 0; i < b->items.size(); ++i) {
+    const su3s_field* di = b->items[i].dest;
+    for (size_t j = 0; j < b->items.size(); ++j) {
+      if (j == i) continue;
+      Canon cj;
+      if (canonicalize(b->items[j].e, &cj)) continue;
+      const su3s_field* dj = b->items[j].dest;
+      bool clash = overlaps(di, dj);
+      for (const su3s_field* f : cj.leaves) clash = clash || overlaps(di, f);
+      if (clash)
+        return fail(SU3S_EINVAL, "batch item %zu writes memory that item %zu reads or writes", i, j);
+    }
+  }
 
   std::vector<BItem> hitems;
   std::vector<BTile> by_tree[kNumBatchTrees];     // plain-load tiles

@@ -298,3 +298,25 @@ def test_neighbour_operation_validation(L):
     assert L.su3s_hop(f32, u4, m2, 0, None) == 6                  # FP64 only
     assert L.su3s_hop(mo, u4, m2, 0, None) == 3                   # lattice
     assert L.su3s_hop(v2, u4, v1, 9, None) == 1                   # arithmetic
+
+
+def test_batch_rejects_items_that_touch_each_other(L):
+    """Batch items run concurrently: an item may not write what another reads."""
+    rc, lat = _lat(L, (2, 2, 2, 2))
+    gap = 1 << 24
+    f = [_wrap(L, lat, su3s.MATRIX, 1, su3s.F64, FAKE + k * gap) for k in range(5)]
+    lv = []
+    for h in f:
+        e = ctypes.c_void_p()
+        assert L.su3s_expr_leaf(h, ctypes.byref(e)) == 0
+        lv.append(e)
+    p01, p23 = ctypes.c_void_p(), ctypes.c_void_p()
+    assert L.su3s_expr_mul(lv[0], lv[1], ctypes.byref(p01)) == 0
+    assert L.su3s_expr_mul(lv[2], lv[3], ctypes.byref(p23)) == 0
+    b = ctypes.c_void_p()
+    assert L.su3s_batch_create(ctypes.byref(b)) == 0
+    assert L.su3s_batch_add(b, f[2], p01) == 0       # item 0 writes f2 ...
+    assert L.su3s_batch_add(b, f[4], p23) == 0       # ... which item 1 reads
+    assert L.su3s_batch_build(b, 0, 0, 0, None) == 1
+    assert b"item" in L.su3s_last_error()
+    assert L.su3s_batch_destroy(b) == 0

@@ -661,3 +661,11 @@ def test_full_size_48_sampled(su3s, math):
         assert np.abs(got - ref).max() < TOL * scale
         del a, b, z
         torch.cuda.empty_cache()
+
+
+def test_empty_batch_builds_and_launches(su3s):
+    b = su3s.Batch()
+    b.build()
+    b.launch()
+    torch.cuda.synchronize()
+    assert b.info() == (0, 0)
