@@ -14,8 +14,8 @@ movement (setup, outside the timed region; --no-tune keeps the defaults).
 convention: every input read once, every output written once) with inputs
 resident in HBM; every field is larger than the 129 MB L2, so no flush is
 needed between steps.  `e2e` runs the same step through the C ABI from pinned
-host buffers (upload + pack, evaluate, unpack + download inside the timed
-region).  `--impl reference` times the CPU oracle on a bounded sample, on every
+host buffers that hold each field in its storage format (upload + layout
+kernel, evaluate, layout kernel + download inside the timed region).  `--impl reference` times the CPU oracle on a bounded sample, on every
 host core (one spawned process per core, each on its own sites).
 
 Multi-GPU (torchrun): every rank runs its own copy of the step (independent
@@ -226,15 +226,15 @@ def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True)
     shared_out = {}
 
     def out_pin(f):
-        # outputs of equal size share a pair of pinned buffers, one per download
-        # stream (downloads on one stream are ordered, so they never overlap)
-        n = int(np.prod(f.canonical_shape))
+        # outputs of equal stored shape share a pair of pinned buffers, one per
+        # download stream (downloads on one stream are ordered, never overlap)
+        key = (f.stored_shape, f.stored_dtype)
         if not with_host:
             return None
-        if n not in shared_out:
-            shared_out[n] = tuple(torch.empty(n, dtype=torch.float64).pin_memory()
-                                  for _ in range(2))
-        return shared_out[n]
+        if key not in shared_out:
+            shared_out[key] = tuple(torch.empty(key[0], dtype=key[1]).pin_memory()
+                                    for _ in range(2))
+        return shared_out[key]
 
     def mk(name, bps, dest, expr, ins, dtype="f64"):
         def run(stream, dest=dest, expr=expr):
@@ -368,14 +368,29 @@ def time_step(rows, torch, stream, steps, warmup, per_row_events=True):
     return total, per_row, launches
 
 
+def stored_host(f, canon, torch):
+    """The pinned host array a user holding field `f` in its storage format
+    has: for FP64 fields the canonical array itself; for reduced precisions the
+    values converted by torch on the host; for two-row formats rows 0 and 1
+    only."""
+    if f.prec == 0 or f.kind == 2:
+        return canon.view(f.stored_shape)
+    x = canon.view((-1,) + tuple(f.canonical_shape[1:]))
+    if f.stored_shape[1] == 6:
+        x = x[:, :2].reshape(-1, 6, 2)
+    return x.reshape(f.stored_shape).to(f.stored_dtype).contiguous().pin_memory()
+
+
 def time_e2e(rows, torch, stream, steps):
-    """The step through the C ABI from pinned host buffers.  Every distinct
-    input field is uploaded (H2D copy + pack kernel) once per step on one of
+    """The step through the C ABI from pinned host buffers, each field held on
+    the host in its storage format.  Every distinct input field is uploaded
+    (H2D copy + layout kernel) once per step on one of
     two upload streams, each row runs on the compute stream as soon as its
     inputs are in, and its outputs are unpacked and copied back on one of two
     download streams; events order them, so host->device copies, kernels and
-    device->host copies of different rows overlap, and a copy does not wait for
-    the previous field's pack or unpack kernel.  Returns (ms per step, H2D
+    device->host copies of different rows (and of consecutive steps) overlap: a
+    field is overwritten only after the previous step's download of it, and a
+    copy does not wait for the previous field's layout kernel.  Returns (ms per step, H2D
     bytes, D2H bytes)."""
     ups = [torch.cuda.Stream(), torch.cuda.Stream()]
     downs = [torch.cuda.Stream(), torch.cuda.Stream()]
@@ -384,9 +399,9 @@ def time_e2e(rows, torch, stream, steps):
     for r in rows:
         for f, h in r.inputs:
             if id(f) not in fields:
-                fields[id(f)] = (f, h)
+                fields[id(f)] = (f, stored_host(f, h, torch))
                 order.append(id(f))
-    last_use = {}
+    last_use, fetched = {}, {}
 
     def one():
         ready = {}
@@ -395,7 +410,7 @@ def time_e2e(rows, torch, stream, steps):
             up = ups[k % 2]
             if fid in last_use:                 # previous step's readers are done with f
                 up.wait_event(last_use[fid])
-            f.upload(h, up)
+            f.upload_stored(h, up)
             ev = torch.cuda.Event()
             ev.record(up)
             ready[fid] = ev
@@ -403,6 +418,9 @@ def time_e2e(rows, torch, stream, steps):
         for r in rows:
             for f, _ in r.inputs:
                 comp.wait_event(ready[id(f)])
+            for f, _ in r.outputs:              # previous step's download of f is done
+                if id(f) in fetched:
+                    comp.wait_event(fetched[id(f)])
             r.run(comp)
             done = torch.cuda.Event()
             done.record(comp)
@@ -412,11 +430,10 @@ def time_e2e(rows, torch, stream, steps):
                 down, buf = downs[nout % 2], h[nout % 2]
                 nout += 1
                 down.wait_event(done)
-                f.download(out=buf, stream=down)
-        for down in downs:                      # outputs reused next step only after download
-            fin = torch.cuda.Event()
-            fin.record(down)
-            comp.wait_event(fin)
+                f.download_stored(out=buf, stream=down)
+                ev = torch.cuda.Event()
+                ev.record(down)
+                fetched[id(f)] = ev
 
     one()
     torch.cuda.synchronize()
@@ -426,11 +443,13 @@ def time_e2e(rows, torch, stream, steps):
         st_.wait_stream(comp)
     for _ in range(steps):
         one()
+    for down in downs:                          # the last step's downloads are in
+        comp.wait_stream(down)
     end.record(comp)
     end.synchronize()
     torch.cuda.synchronize()
-    h2d = sum(fields[fid][1].numel() * 8 for fid in order)
-    d2h = sum(h[0].numel() * 8 for r in rows for _, h in r.outputs)
+    h2d = sum(fields[fid][1].numel() * fields[fid][1].element_size() for fid in order)
+    d2h = sum(h[0].numel() * h[0].element_size() for r in rows for _, h in r.outputs)
     return start.elapsed_time(end) / steps, h2d, d2h
 
 
@@ -734,7 +753,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true",

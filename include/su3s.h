@@ -176,6 +176,29 @@ int su3s_field_download(const su3s_field* f, double* host_canonical, size_t n_do
 int su3s_field_download_static(const su3s_field* f, double* host_canonical, size_t n_doubles,
                                void* stream);
 
+/* Stored-format transfer (the paper has no counterpart: a service of the
+ * library for callers that hold data in a reduced storage format).  The host
+ * array is site-major like the canonical one, but each (site, link) object
+ * holds only its stored complex components (9 for a matrix, rows 0 and 1 =
+ * 6 for a C12 matrix, 3 for a vector; 1 real for a real field), each in the
+ * field's storage format: (re, im) pairs of doubles (F64, F64_C12), floats
+ * (F32, F32_C12), bfloat16 or binary16 values (BF16, F16); reals are doubles.
+ * Element ((s*nmu + mu)*ncomp + c) is component c of link mu at site s.  The
+ * bytes are moved as they are: no rounding, no widening, no row rebuilt, so a
+ * download after an upload returns the same bytes, and a C12 download gives
+ * the two stored rows.  su3s_field_stored_bytes gives the array's size. */
+int su3s_field_stored_bytes(const su3s_field* f, size_t* bytes);
+
+/* Upload a stored-format host array of nbytes bytes (must equal
+ * su3s_field_stored_bytes) into the field; pad sites are set to zero.  Staging
+ * as in su3s_field_upload.  EINVAL on a null argument, ESHAPE on a wrong size,
+ * ENOMEM if staging fails. */
+int su3s_field_upload_stored(su3s_field* f, const void* host_stored, size_t nbytes, void* stream);
+
+/* Download the field to a stored-format host array of nbytes bytes.  Errors
+ * and ordering as su3s_field_upload_stored / su3s_field_download. */
+int su3s_field_download_stored(const su3s_field* f, void* host_stored, size_t nbytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * Expressions (Sec. 3, Listing 1: the expression-template tree)
  * ---------------------------------------------------------------------- */

@@ -71,6 +71,9 @@ def load(build_if_missing=False):
         "su3s_field_upload": ([P, P, SZ, P], I),
         "su3s_field_download": ([P, P, SZ, P], I),
         "su3s_field_download_static": ([P, P, SZ, P], I),
+        "su3s_field_stored_bytes": ([P, ctypes.POINTER(SZ)], I),
+        "su3s_field_upload_stored": ([P, P, SZ, P], I),
+        "su3s_field_download_stored": ([P, P, SZ, P], I),
         "su3s_expr_leaf": ([P, PP], I),
         "su3s_expr_mul": ([P, P, PP], I),
         "su3s_expr_add": ([P, P, PP], I),
@@ -263,6 +266,56 @@ class Field:
                                                _stream(stream)))
         (torch.cuda.current_stream() if stream is None else stream).synchronize()
         return res
+
+    @property
+    def stored_shape(self):
+        """Shape of the stored-format host array: (V*nmu, ncomp, 2) (ncomp = 9,
+        6 for two-row matrices, 3 for vectors) or (V*nmu,) for reals."""
+        if self.kind == REAL:
+            return (self.lattice.volume * self.nmu,)
+        nc = 3 if self.kind == VECTOR else 6 if self.prec in (F64_C12, F32_C12) else 9
+        return (self.lattice.volume * self.nmu, nc, 2)
+
+    @property
+    def stored_dtype(self):
+        """torch dtype of one stored real of the field."""
+        import torch
+        if self.kind == REAL:
+            return torch.float64
+        return {F64: torch.float64, F64_C12: torch.float64, F32: torch.float32,
+                F32_C12: torch.float32, BF16: torch.bfloat16, F16: torch.float16}[self.prec]
+
+    def _check_stored(self, t):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("stored-format array must be a contiguous CPU tensor (got %s, "
+                             "shape %s, strides %s)" % (t.device, tuple(t.shape), t.stride()))
+        if t.dtype != self.stored_dtype or tuple(t.shape) != self.stored_shape:
+            raise ValueError("stored-format array is %s %s; the field needs %s %s"
+                             % (t.dtype, tuple(t.shape), self.stored_dtype, self.stored_shape))
+
+    def upload_stored(self, host, stream=None):
+        """Copy a stored-format CPU tensor (`stored_shape`, `stored_dtype`; pinned
+        for an asynchronous copy) into the field, bytes unchanged."""
+        import torch
+        self._check_stored(host)
+        _check(_lib.su3s_field_upload_stored(self._h, ctypes.c_void_p(host.data_ptr()),
+                                             host.numel() * host.element_size(), _stream(stream)))
+        if not host.is_pinned():
+            (torch.cuda.current_stream() if stream is None else stream).synchronize()
+
+    def download_stored(self, out=None, stream=None):
+        """The field's stored bytes as a CPU tensor (`stored_shape`, `stored_dtype`);
+        synchronous unless `out` is a pinned CPU tensor and a stream is given."""
+        import torch
+        sync = out is None
+        if out is None:
+            out = torch.empty(self.stored_shape, dtype=self.stored_dtype)
+        self._check_stored(out)
+        _check(_lib.su3s_field_download_stored(self._h, ctypes.c_void_p(out.data_ptr()),
+                                               out.numel() * out.element_size(), _stream(stream)))
+        if sync:
+            (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        return out
 
     def pack(self, dev_canonical, stream=None):
         """Fill the field from a canonical float64 CUDA tensor."""

@@ -691,6 +691,55 @@ SU3S_EXPORT int su3s_field_download(const su3s_field* f, double* host, size_t n,
   return ok();
 }
 
+static size_t stored_bytes(const su3s_field* f) {
+  return (size_t)f->V * f->nmu * f->ncomp * f->elem_bytes;
+}
+
+SU3S_EXPORT int su3s_field_stored_bytes(const su3s_field* f, size_t* bytes) {
+  if (!f || !bytes) return fail(SU3S_EINVAL, "null argument");
+  *bytes = stored_bytes(f);
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_upload_stored(su3s_field* f, const void* host, size_t nbytes, void* stream) {
+  if (!f || !host) return fail(SU3S_EINVAL, "null argument");
+  if (nbytes != stored_bytes(f))
+    return fail(SU3S_ESHAPE, "host array has %zu bytes, the field stores %zu", nbytes, stored_bytes(f));
+  cudaStream_t st = (cudaStream_t)stream;
+  void* stage = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (nbytes > 0) {
+    e = scratch_alloc(&stage, nbytes, st);
+    if (e != cudaSuccess) return fail(SU3S_ENOMEM, "staging allocation of %zu bytes failed: %s",
+                                      nbytes, cudaGetErrorString(e));
+    e = cudaMemcpyAsync(stage, host, nbytes, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = launch_put_stored(f, stage, st);
+  cudaError_t e2 = stage ? scratch_free(stage, st) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "stored upload");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "upload staging release");
+  return ok();
+}
+
+SU3S_EXPORT int su3s_field_download_stored(const su3s_field* f, void* host, size_t nbytes,
+                                           void* stream) {
+  if (!f || !host) return fail(SU3S_EINVAL, "null argument");
+  if (nbytes != stored_bytes(f))
+    return fail(SU3S_ESHAPE, "host array has %zu bytes, the field stores %zu", nbytes, stored_bytes(f));
+  if (nbytes == 0) return ok();
+  cudaStream_t st = (cudaStream_t)stream;
+  void* stage = nullptr;
+  cudaError_t e = scratch_alloc(&stage, nbytes, st);
+  if (e != cudaSuccess) return fail(SU3S_ENOMEM, "staging allocation of %zu bytes failed: %s",
+                                    nbytes, cudaGetErrorString(e));
+  e = launch_get_stored(f, stage, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, stage, nbytes, cudaMemcpyDeviceToHost, st);
+  cudaError_t e2 = scratch_free(stage, st);
+  if (e != cudaSuccess) return cuda_fail(e, "stored download");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "download staging release");
+  return ok();
+}
+
 // ----------------------------------------------------------- expressions
 static int new_node(int op, int kind, const su3s_expr* a, const su3s_expr* b, su3s_field* f,
                     double s, su3s_expr** out) {

@@ -106,6 +106,8 @@ int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, 
 // pack / unpack kernels
 cudaError_t launch_pack(const su3s_field* f, const double* canon, cudaStream_t st);
 cudaError_t launch_unpack(const su3s_field* f, double* canon, cudaStream_t st);
+cudaError_t launch_put_stored(const su3s_field* f, const void* src, cudaStream_t st);
+cudaError_t launch_get_stored(const su3s_field* f, void* dst, cudaStream_t st);
 
 // stream-ordered scratch from the library's memory pool
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);

@@ -86,6 +86,38 @@ __global__ void k_unpack_c12(FieldDesc d, double* __restrict__ canon, int64_t V,
   }
 }
 
+// Stored-format transfer.  The compact array is site-major like the canonical
+// one, but holds per (site, link) only the ncomp stored elements (two rows of a
+// C12 matrix), each as the field stores it (T = one element's bytes).  Element
+// q = ((s*nmu + mu)*ncomp + c); elements past V*nmu*ncomp are the pad sites,
+// which the put kernel zeroes.
+template <typename T>
+__global__ void k_put_stored(FieldDesc d, const T* __restrict__ src, int64_t V, int64_t Vpad, int nmu,
+                             int nc) {
+  const int64_t n = V * nmu * nc, np = Vpad * nmu * nc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += stride) {
+    const int c = (int)(q % nc);
+    const int64_t m = q / nc;
+    const int mu = (int)(m % nmu);
+    const int64_t s = m / nmu;
+    reinterpret_cast<T*>(d.ptr)[fbase(d, s, mu) + c * d.s_c] = q < n ? src[q] : T{};
+  }
+}
+
+template <typename T>
+__global__ void k_get_stored(FieldDesc d, T* __restrict__ dst, int64_t V, int nmu, int nc) {
+  const int64_t n = V * nmu * nc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+    const int c = (int)(q % nc);
+    const int64_t m = q / nc;
+    const int mu = (int)(m % nmu);
+    const int64_t s = m / nmu;
+    dst[q] = reinterpret_cast<const T*>(d.ptr)[fbase(d, s, mu) + c * d.s_c];
+  }
+}
+
 static dim3 grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   int64_t cap = (int64_t)sm_count() * 32;
@@ -140,6 +172,37 @@ cudaError_t launch_unpack(const su3s_field* f, double* canon, cudaStream_t st) {
     case SU3S_F16: return unpack_t<P_F16>(f, canon, st);
     case SU3S_F64_C12: return unpack_t<P_F64_C12>(f, canon, st);
     default: return unpack_t<P_F32_C12>(f, canon, st);
+  }
+}
+
+template <typename T>
+static cudaError_t put_stored_t(const su3s_field* f, const void* src, cudaStream_t st) {
+  const int64_t np = f->Vpad * f->nmu * f->ncomp;
+  if (np > 0)
+    k_put_stored<T><<<grid_for(np), 256, 0, st>>>(f->desc, (const T*)src, f->V, f->Vpad, f->nmu, f->ncomp);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t get_stored_t(const su3s_field* f, void* dst, cudaStream_t st) {
+  const int64_t n = f->V * f->nmu * f->ncomp;
+  if (n > 0) k_get_stored<T><<<grid_for(n), 256, 0, st>>>(f->desc, (T*)dst, f->V, f->nmu, f->ncomp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_put_stored(const su3s_field* f, const void* src, cudaStream_t st) {
+  switch (f->elem_bytes) {
+    case 16: return put_stored_t<uint4>(f, src, st);
+    case 8: return put_stored_t<uint2>(f, src, st);
+    default: return put_stored_t<uint32_t>(f, src, st);
+  }
+}
+
+cudaError_t launch_get_stored(const su3s_field* f, void* dst, cudaStream_t st) {
+  switch (f->elem_bytes) {
+    case 16: return get_stored_t<uint4>(f, dst, st);
+    case 8: return get_stored_t<uint2>(f, dst, st);
+    default: return get_stored_t<uint32_t>(f, dst, st);
   }
 }
 

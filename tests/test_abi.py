@@ -320,3 +320,26 @@ def test_batch_rejects_items_that_touch_each_other(L):
     assert L.su3s_batch_build(b, 0, 0, 0, None) == 1
     assert b"item" in L.su3s_last_error()
     assert L.su3s_batch_destroy(b) == 0
+
+
+@pytest.mark.parametrize("kind,prec,ncomp,eb", [
+    (su3s.MATRIX, su3s.F64, 9, 16), (su3s.MATRIX, su3s.F32, 9, 8), (su3s.MATRIX, su3s.BF16, 9, 4),
+    (su3s.MATRIX, su3s.F16, 9, 4), (su3s.MATRIX, su3s.F64_C12, 6, 16),
+    (su3s.MATRIX, su3s.F32_C12, 6, 8), (su3s.VECTOR, su3s.BF16, 3, 4), (su3s.REAL, su3s.F64, 1, 8)])
+def test_stored_transfer_sizes_and_validation(L, kind, prec, ncomp, eb):
+    """The stored-format array has V*nmu*ncomp elements of the stored size (no
+    padding); a wrong size or a null pointer is refused before any copy."""
+    rc, lat = _lat(L, (3, 2, 1, 5))   # V = 30
+    for nmu in (1, 4):
+        h = _wrap(L, lat, kind, nmu, prec, FAKE)
+        n = ctypes.c_size_t()
+        assert L.su3s_field_stored_bytes(h, ctypes.byref(n)) == 0
+        assert n.value == 30 * nmu * ncomp * eb
+        buf = ctypes.create_string_buffer(n.value + 16)
+        assert L.su3s_field_upload_stored(h, buf, n.value - eb, None) == 3
+        assert L.su3s_field_download_stored(h, buf, n.value + eb, None) == 3
+        assert b"stores" in L.su3s_last_error()
+        assert L.su3s_field_upload_stored(h, None, n.value, None) == 1
+        assert L.su3s_field_download_stored(None, buf, n.value, None) == 1
+        assert L.su3s_field_stored_bytes(h, None) == 1
+        assert L.su3s_field_destroy(h) == 0

@@ -346,6 +346,86 @@ def test_pack_zeroes_pad_sites(su3s):
     assert not torch.isnan(t[:, :30, :]).any()
 
 
+STORED = [(0, None, torch.float64), (1, "f32", torch.float32), (2, "bf16", torch.bfloat16),
+          (3, "f16", torch.float16), (4, None, torch.float64), (5, "f32", torch.float32)]
+
+
+def stored_of(arr, prec, fmt, dtype, kind):
+    """Stored-format array of canonical `arr` computed from the oracle: rows 0,1
+    for the two-row formats, values rounded to the storage format."""
+    x = arr
+    if prec in (4, 5):
+        x = arr[:, :2].reshape(arr.shape[0], 6, 2)
+    if fmt is not None:
+        x = oracle.round_to(x, fmt)
+    x = np.ascontiguousarray(x).reshape(arr.shape[0], -1, 2)
+    return torch.from_numpy(x).to(dtype)   # exact: the values fit the format
+
+
+@pytest.mark.parametrize("prec,fmt,dtype", STORED, ids=["f64", "f32", "bf16", "f16", "f64c12", "f32c12"])
+@pytest.mark.parametrize("lay", LAYOUTS, ids=layout_id)
+def test_stored_format_transfer(su3s, prec, fmt, dtype, lay):
+    """Stored-format download of a packed field equals the oracle's rounding
+    (bitwise); a stored-format upload unpacks to the oracle's widening (and row
+    rebuild) and downloads to the same bytes."""
+    dims = (3, 2, 1, 5)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED + 7, nmu=4, names=("a", "v"))
+    cases = [(su3s.MATRIX, f["a"])] + ([] if prec >= 4 else [(su3s.VECTOR, f["v"])])
+    for kind, arr in cases:
+        x = upload(su3s, lat, arr, kind=kind, nmu=4, prec=prec, layout=lay[1], block=lay[2])
+        want = stored_of(arr, prec, fmt, dtype, kind)
+        got = x.download_stored()
+        assert got.dtype == dtype and tuple(got.shape) == x.stored_shape
+        assert torch.equal(got.view(torch.uint8), want.view(torch.uint8))
+        y = x.like()
+        y.tensor.fill_(255 if y.tensor.dtype == torch.uint8 else float("nan"))
+        y.upload_stored(want)
+        assert torch.equal(y.download_stored().view(torch.uint8), want.view(torch.uint8))
+        canon = want.double().numpy()
+        if prec in (4, 5):
+            # rows 0,1 exact; row 2 rebuilt in FP64: each real part is a sum of
+            # four products of values of modulus <= 1, so contraction and
+            # summation order move it by at most 8 * 2^-53
+            canon = oracle.c12_expand(canon.reshape(-1, 2, 3, 2))
+            got = y.download()
+            assert np.array_equal(got[:, :2], canon[:, :2])
+            assert np.abs(got[:, 2] - canon[:, 2]).max() <= 8 * 2.0 ** -53
+        else:
+            assert np.array_equal(y.download(), canon.reshape(arr.shape))
+        assert torch.equal(y.tensor, x.tensor)     # pad sites zeroed, same layout bytes
+
+
+@pytest.mark.parametrize("prec,dtype", [(0, torch.float64), (2, torch.bfloat16), (5, torch.float32)],
+                         ids=["f64", "bf16", "f32c12"])
+def test_stored_transfer_moves_bytes_unchanged(su3s, prec, dtype):
+    """Arbitrary bit patterns (NaN payloads, infinities, subnormals) survive an
+    upload and download in the stored format."""
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    x = su3s.Field(lat, su3s.MATRIX, 1, prec, su3s.AOSOA, 32)
+    g = torch.Generator().manual_seed(SEED)
+    nbytes = int(np.prod(x.stored_shape)) * torch.empty(0, dtype=dtype).element_size()
+    raw = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, generator=g)
+    host = raw.view(dtype).view(x.stored_shape).pin_memory()
+    st = torch.cuda.Stream()
+    x.upload_stored(host, stream=st)
+    out = torch.empty_like(host).pin_memory()
+    x.download_stored(out=out, stream=st)
+    st.synchronize()
+    assert torch.equal(out.reshape(-1).view(torch.uint8), raw)
+
+
+def test_stored_transfer_real_field(su3s):
+    dims = (3, 2, 1, 5)
+    lat = su3s.Lattice(dims)
+    r = synth.uniform_real(SEED, 3, 30 * 2)
+    x = su3s.Field(lat, su3s.REAL, 2, su3s.F64, su3s.SOA)
+    x.upload_stored(torch.from_numpy(r))
+    assert np.array_equal(x.download(), r)
+    assert torch.equal(x.download_stored(), torch.from_numpy(r))
+
+
 # ---------------------------------------------------------- reverse mode
 @pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("name,tree", [("MM", ("mul", ("leaf", "a"), ("leaf", "b"))), ("E1", E1),
