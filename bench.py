@@ -53,6 +53,9 @@ MATH_NAMES = ("fx", "df32", "f64")
 MATH_IDS = {"f64": 1, "df32": 2, "fx": 3}
 MATH_DESC = {"fx": "shared-exponent fixed-point (fx)", "df32": "pair-of-FP32 (df32)",
              "f64": "native FP64 (f64)"}
+# arithmetic type of the rows with FP64 storage under each arithmetic
+MATH_DTYPE = {"fx": "int64", "df32": "df32", "f64": "f64"}
+MATH_ERR = {"fx": "7.8e-16 - 1.4e-15", "df32": "3.6e-14 - 5.7e-14", "f64": "3.3e-16 - 6.7e-16"}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on a
 # 32^4 lattice (1,048,576 sites; the batch row: its 64 fixed lattices), from one
@@ -502,6 +505,25 @@ def _oracle_pass_worker(job):
     return reps * bytes_one, t0, time.time(), reps
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_sample(budget_s=12.0, frac_sites=1 << 16, procs=None):
     """The oracle, as it stands (single-threaded C), on a bounded sample of the
     step, on the host's cores: `procs` spawned processes (default: every core
@@ -521,6 +543,7 @@ def cpu_oracle_sample(budget_s=12.0, frac_sites=1 << 16, procs=None):
     span = max(r[2] for r in res) - min(r[1] for r in res)
     passes = sum(r[3] for r in res)
     return {"value": total / span / 1e9, "unit": "GB/s", "cores": procs, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": "every row of the step on %d x %d sites (%d processes, %d passes in %.1f s)"
                       % (procs, frac_sites, procs, passes, span),
             "seconds": span, "passes": passes}
@@ -798,7 +821,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": "48^4 lattice, every hot-path row (A2-A9), CPU oracle on a "
                                        "bounded sample of sites"},
-                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu")},
                 "e2e": {"value": round(cb["value"], 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -854,7 +877,9 @@ def main():
     row_out = []
     for r, ms in zip(rows, per_row):
         m = float(np.mean(ms))
-        row_out.append({"row": r.name, "dtype": r.dtype, "ms": round(m, 5),
+        row_out.append({"row": r.name, "storage": r.dtype,
+                        "arith": MATH_DTYPE[args.math] if r.dtype.startswith("f64") else "f32",
+                        "ms": round(m, 5),
                         "GB_s": round(r.nbytes / (m * 1e-3) / 1e9, 1),
                         "Gsites_s": round(r.sites / (m * 1e-3) / 1e9, 3)})
     peak, peak_kind = read_peaks()
@@ -893,18 +918,23 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_oracle_sample()
-        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu")}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": MATH_DTYPE[args.math], "data": "synthetic",
             "config": {"workload": ("48^4 lattice (5,308,416 sites), every hot-path row A2-A9 once "
                                     "per step; FP64 rows in %s arithmetic" % MATH_DESC[args.math]
                                     if full else "subset %s on %s" % (args.rows or "all rows",
                                                                       "x".join(map(str, dims)))),
+                       "storage": "f64 (A2-A5, A7 two-row, A8, A9); f32/bf16/f16 (A6); "
+                                  "two-row f32 (A7)",
+                       "arithmetic": ("FP64-storage rows in %s, max abs error %s against the FP64 "
+                                      "oracle (bound 1e-13); reduced-precision rows in FP32"
+                                      % (MATH_DESC[args.math], MATH_ERR[args.math])),
                        "lattice": list(dims), "layout": "soa", "pipeline": args.pipeline,
                        "tuned": not args.no_tune,
                        "l2": "every field larger than the 129 MB L2; no flush needed",
