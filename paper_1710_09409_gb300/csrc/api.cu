@@ -395,6 +395,9 @@ static void encode_tmap(su3s_field* f) {
   if (!enc) return;
   const uint64_t w = (uint64_t)f->desc.s_c;
   const uint64_t rows = (uint64_t)f->Vpad * f->nmu * f->ncomp / w;
+  // tensor-copy coordinates are signed 32-bit: column 2*site (box end 2*w-1)
+  // and row; larger fields (SoA beyond 2^30 sites) use the plain-load kernels
+  if (2 * w > (1ull << 31) || rows > (1ull << 31)) return;
   const cuuint64_t dims[2] = {2 * w, rows};
   const cuuint64_t strides[1] = {w * 16};
   const cuuint32_t box[2] = {64, (cuuint32_t)f->ncomp};

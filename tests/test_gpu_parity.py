@@ -743,6 +743,47 @@ def test_full_size_48_sampled(su3s, math):
         torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("dims", [(128, 128, 128, 512), (128, 128, 128, 513)],
+                         ids=["V=2^30", "V>2^30"])
+def test_largest_soa_fields(su3s, dims):
+    """z = a*v into v on the largest lattices the device holds: at V = 2^30 the
+    staged kernels copy at tensor column 2^31 - 64, the top of the signed
+    32-bit coordinate range; beyond it the fields take the plain-load kernels.
+    A 155 GB Gaussian matrix field and a 52 GB vector field (seeded on the
+    device); sampled sites, the sites around 2^30 and the last site are checked
+    against the oracle."""
+    v = synth.volume(dims)
+    need = v * (144 + 48)
+    if torch.cuda.mem_get_info()[0] < need + (4 << 30):
+        pytest.skip("needs %.0f GB of free device memory" % (need / 1e9))
+    lat = su3s.Lattice(dims)
+    a = su3s.Field(lat, su3s.MATRIX, 1, su3s.F64, su3s.SOA)
+    x = su3s.Field(lat, su3s.VECTOR, 1, su3s.F64, su3s.SOA)
+    g = torch.Generator(device="cuda").manual_seed(SEED)
+    a.tensor.normal_(generator=g)
+    x.tensor.normal_(generator=g)
+    vpad = a.tensor.numel() // 18
+    rng = np.random.default_rng(5)
+    edge = [0, 1, (1 << 30) - 33, (1 << 30) - 32, (1 << 30) - 1, v - 33, v - 32, v - 1]
+    sample = np.unique(np.concatenate([rng.choice(v, 4000, replace=False), edge]))
+    sample = sample[sample < v]
+    idx = torch.from_numpy(sample).cuda()
+
+    def gather(f, nc):
+        t = f.tensor.view(nc, vpad, 2)[:, idx, :].permute(1, 0, 2).contiguous()
+        return t.cpu().numpy().reshape((-1, 3, 3, 2) if nc == 9 else (-1, 3, 2))
+    ha, hx = gather(a, 9), gather(x, 3)
+    su3s.evaluate(x, a * x)
+    got = gather(x, 3)
+    torch.cuda.synchronize()
+    del a, x
+    torch.cuda.empty_cache()
+    ref = oracle.mv(ha, hx)
+    scale = np.einsum("nij,nj->ni", np.abs(cplx(ha)), np.abs(cplx(hx)))
+    err = np.abs(cplx(got) - cplx(ref))
+    assert (err <= TOL * np.maximum(1.0, 2 * scale)).all()
+
+
 def test_empty_batch_builds_and_launches(su3s):
     b = su3s.Batch()
     b.build()
