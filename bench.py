@@ -172,6 +172,37 @@ class Row:
         self.tune = None   # callable(stream) -> (threads, blocks/SM, variant, ms), forward rows
 
 
+def out_buf_bytes(dims):
+    """Largest output of the step: the Lorentz product, 4 FP64 matrices per site."""
+    v = 1
+    for x in dims:
+        v *= x
+    return 4 * 144 * v
+
+
+def e2e_host_bytes(dims):
+    """Pinned host memory one rank's end-to-end run holds: the canonical FP64
+    inputs (a, b, c, d, W: 144 B per site each; v 48; the two Lorentz fields
+    576 each), the stored copies of the reduced-precision and two-row inputs
+    (576 B per site in all), the 64 batch lattices (4 FP64 matrix fields over
+    their 6.2 M sites) and two output buffers of the largest output."""
+    v = 1
+    for x in dims:
+        v *= x
+    batch = 4 * 144 * sum(int(np.prod(s)) * 13 for s in BATCH_SHAPES)   # ~64 lattices
+    return (5 * 144 + 48 + 2 * 576 + 576) * v + batch + 2 * out_buf_bytes(dims)
+
+
+def host_mem_available():
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
 def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True):
     """Allocate fields, fill them from the seeded generator, return the rows
     whose names pass `want`."""
@@ -229,15 +260,17 @@ def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True)
     shared_out = {}
 
     def out_pin(f):
-        # outputs of equal stored shape share a pair of pinned buffers, one per
-        # download stream (downloads on one stream are ordered, never overlap)
-        key = (f.stored_shape, f.stored_dtype)
+        # every output is downloaded into one of two pinned byte buffers (one
+        # per download stream: downloads on one stream are ordered, so they
+        # never overlap), viewed with the output's stored shape and dtype
         if not with_host:
             return None
-        if key not in shared_out:
-            shared_out[key] = tuple(torch.empty(key[0], dtype=key[1]).pin_memory()
-                                    for _ in range(2))
-        return shared_out[key]
+        nb = int(np.prod(f.stored_shape)) * torch.empty(0, dtype=f.stored_dtype).element_size()
+        if not shared_out or shared_out["bytes"] < nb:
+            cap = max(nb, out_buf_bytes(dims))
+            shared_out.update(bytes=cap, bufs=[torch.empty(cap, dtype=torch.uint8).pin_memory()
+                                               for _ in range(2)])
+        return tuple(b[:nb].view(f.stored_dtype).view(f.stored_shape) for b in shared_out["bufs"])
 
     def mk(name, bps, dest, expr, ins, dtype="f64"):
         def run(stream, dest=dest, expr=expr):
@@ -846,6 +879,15 @@ def main():
                        "tma_leaf": su3s.PIPE_TMA_LEAF, "tma_ring": su3s.PIPE_TMA_RING}[args.pipeline])
     stream = torch.cuda.Stream()
     with_host = not args.no_e2e
+    e2e_skip = None
+    if with_host:
+        # every rank on this node pins its own host buffers
+        lws = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+        need, avail = e2e_host_bytes(dims) * lws, host_mem_available()
+        if avail is not None and need > 0.85 * avail:
+            with_host = False
+            e2e_skip = ("host memory: %d ranks need %.0f GB pinned, %.0f GB available"
+                        % (lws, need / 1e9, avail / 1e9))
     rows, keep = build_rows(su3s, synth, torch, with_host, dims, want)
     torch.cuda.synchronize()
     tuned = []
@@ -908,7 +950,7 @@ def main():
                                  "GB_s": round(r.nbytes / (m * 1e-3) / 1e9, 1)})
     su3s.set_default_math(MATH_IDS[args.math])
 
-    e2e = None
+    e2e = {"value": None, "unit": "GB/s", "unavailable": e2e_skip} if e2e_skip else None
     if with_host:
         e_ms, h2d, d2h = time_e2e(rows, torch, stream, args.e2e_steps)
         e_ms = max_over_ranks(e_ms, dist, "cuda")

@@ -15,7 +15,7 @@ import torch
 
 import oracle
 import synth
-from helpers import E1, E2, E3, cplx, lattice_fields
+from helpers import BOUND_VS_F64, E1, E2, E3, ULP, cplx, lattice_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -240,10 +240,6 @@ def test_real_field_trees_random(su3s):
 
 
 # ---------------------------------------------------------- reduced precision
-ULP = {"f32": lambda x: np.spacing(np.abs(x).astype(np.float32)).astype(np.float64),
-       "f16": lambda x: np.spacing(np.abs(x).astype(np.float16)).astype(np.float64),
-       "bf16": lambda x: 2.0 ** (np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** -126))) - 7)}
-BOUND_VS_F64 = {"f32": 2e-6, "f16": 3e-3, "bf16": 2.5e-2}
 
 
 @pytest.mark.parametrize("fmt", ["f32", "bf16", "f16"])
