@@ -94,6 +94,28 @@ __device__ __forceinline__ void load_nc(const FieldDesc& f, int64_t s, int mu, t
   M::template normalize_obj<W>(out);
 }
 
+// Link U_mu(s) (dag false) or its adjoint U_mu(s)^dagger (dag true), in the
+// arithmetic M.  The adjoint is taken in the load: element (i, j) is read from
+// component (j, i) and its imaginary part's sign bit is flipped, so one product
+// routine serves the forward and the backward terms.
+template <class M>
+__device__ __forceinline__ void load_link(const FieldDesc& f, int64_t s, int mu, bool dag,
+                                          typename M::R* out) {
+  const int64_t b = elem_base(f, s, mu);
+  const uint4* p = reinterpret_cast<const uint4*>(f.ptr);
+  const uint32_t sg = dag ? 0x80000000u : 0u;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int c = 3 * i + j;
+      const uint4 v = __ldg(p + b + (dag ? 3 * j + i : c) * f.s_c);
+      out[2 * c] = M::from_bits(v.x, v.y);
+      out[2 * c + 1] = M::from_bits(v.z, v.w ^ sg);
+    }
+  M::template normalize_obj<18>(out);
+}
+
 // Site of s + shift e_mu for a runtime direction (the geometry is selected,
 // not indexed, so it stays in registers).
 __device__ __forceinline__ int64_t shift_site_rt(const LatGeo& g, int64_t s, int mu, int shift) {
@@ -106,39 +128,55 @@ __device__ __forceinline__ int64_t shift_site_rt(const LatGeo& g, int64_t s, int
 }
 
 // One thread per site; the grid is one wave, so the sites in flight (and the
-// backward links and neighbours they share) fit the L2 cache; the loop over
-// directions is not unrolled, which keeps the code a quarter as large.
+// backward links and neighbours they share) fit the L2 cache, and the loop over
+// the 8 terms is rolled.  Colour matrices: the terms run through a single
+// product routine (the backward link's adjoint is taken in its load), which
+// keeps the matrix-product code small enough for the instruction cache (+29%
+// at 48^4 over separate forward and backward routines).  Colour vectors: the
+// matrix-vector code is small, and separate forward and backward routines,
+// with the first term opening the accumulators, are faster (+13%).
 template <class M, int KIND>
 __global__ void __launch_bounds__(128) k_hop(FieldDesc dst, FieldDesc U, FieldDesc v, LatGeo g) {
   constexpr int W = KIND == KM ? 18 : 6;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.V;
        s += (int64_t)gridDim.x * blockDim.x) {
     typename M::A acc[W];
-    {
-      // mu = 0 forward term opens the accumulators
-      typename M::R u[18], x[W];
-      load_nc<M, 18>(U, s, 0, u);
-      load_nc<M, W>(v, shift_site_rt(g, s, 0, 1), 0, x);
-      if constexpr (KIND == KM) mm_acc<M, true, 1, false, false>(acc, u, x);
-      else mv_acc<M, true, 1, false>(acc, u, x);
-    }
+    if constexpr (KIND == KM) {
+#pragma unroll
+      for (int r = 0; r < W; ++r) acc[r] = M::zero();
 #pragma unroll 1
-    for (int t = 1; t < 8; ++t) {
-      // t = 2 mu: forward U_mu(x) v(x + mu); t = 2 mu + 1: backward
-      // U_mu(x - mu)^dagger v(x - mu), the link read transposed
-      const int mu = t >> 1;
-      typename M::R u[18], x[W];
-      if ((t & 1) == 0) {
-        load_nc<M, 18>(U, s, mu, u);
-        load_nc<M, W>(v, shift_site_rt(g, s, mu, 1), 0, x);
-        if constexpr (KIND == KM) mm_combine<M, 1, false, false>(acc, u, x);
-        else mv_combine<M, 1, false>(acc, u, x);
-      } else {
-        const int64_t bw = shift_site_rt(g, s, mu, -1);
-        load_nc<M, 18>(U, bw, mu, u);
-        load_nc<M, W>(v, bw, 0, x);
-        if constexpr (KIND == KM) mm_combine<M, 1, true, false>(acc, u, x);
-        else mv_combine<M, 1, true>(acc, u, x);
+      for (int t = 0; t < 8; ++t) {
+        // t = 2 mu: forward U_mu(x) v(x + mu); t = 2 mu + 1: backward
+        // U_mu(x - mu)^dagger v(x - mu)
+        const int mu = t >> 1;
+        const bool bwd = (t & 1) != 0;
+        const int64_t n = shift_site_rt(g, s, mu, bwd ? -1 : 1);
+        typename M::R u[18], x[W];
+        load_link<M>(U, bwd ? n : s, mu, bwd, u);
+        load_nc<M, W>(v, n, 0, x);
+        mm_combine<M, 1, false, false>(acc, u, x);
+      }
+    } else {
+      {
+        typename M::R u[18], x[W];
+        load_nc<M, 18>(U, s, 0, u);
+        load_nc<M, W>(v, shift_site_rt(g, s, 0, 1), 0, x);
+        mv_acc<M, true, 1, false>(acc, u, x);
+      }
+#pragma unroll 1
+      for (int t = 1; t < 8; ++t) {
+        const int mu = t >> 1;
+        typename M::R u[18], x[W];
+        if ((t & 1) == 0) {
+          load_nc<M, 18>(U, s, mu, u);
+          load_nc<M, W>(v, shift_site_rt(g, s, mu, 1), 0, x);
+          mv_combine<M, 1, false>(acc, u, x);
+        } else {
+          const int64_t bw = shift_site_rt(g, s, mu, -1);
+          load_nc<M, 18>(U, bw, mu, u);
+          load_nc<M, W>(v, bw, 0, x);
+          mv_combine<M, 1, true>(acc, u, x);
+        }
       }
     }
     typename M::A out[1][W];
