@@ -345,6 +345,11 @@ def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True)
     rows.append(Row(ROW_A8, B_E1 * bsites, bsites, run_batch, bins, bouts))
     rows[-1].keep = (batch, keep)
 
+    def tune_batch(stream):
+        th, tile, bps, ms = batch.tune(su3s.MATH_DEFAULT, stream)
+        return {"threads": th, "blocks_per_sm": bps, "tile_sites": tile, "ms": round(ms, 5)}
+    rows[-1].tune = tune_batch
+
     return _adjoint_rows(su3s, rows, want, v, Fd, Fw, P, out_pin), {"lat": lat}
 
 
@@ -894,7 +899,11 @@ def main():
     if not args.no_tune:
         for r in rows:
             if r.tune is not None:
-                th, bps, var, tms = r.tune(stream)
+                res = r.tune(stream)
+                if isinstance(res, dict):       # the batch: its own launch parameters
+                    tuned.append(dict(row=r.name, **res))
+                    continue
+                th, bps, var, tms = res
                 tuned.append({"row": r.name, "threads": th, "blocks_per_sm": bps,
                               "variant": var, "ms": round(tms, 5)})
         torch.cuda.synchronize()

@@ -310,9 +310,10 @@ int su3s_set_pipeline(int mode);
 int su3s_device_error(int* code, void* stream);
 
 /* Autotune the launch geometry for `e` into `dest`: times each candidate
- * (data movement 0/1/2 as for su3s_set_pipeline, threads 64..256, full or
+ * (data movement 0..3 as for su3s_set_pipeline, threads 64..256, full or
  * grid-stride grids) with CUDA events on `stream` (synchronising it; dest is
- * overwritten), keeps the fastest for later su3s_eval calls and reports it in
+ * overwritten, so a dest that is one of the leaves changes that leaf), keeps
+ * the fastest for later su3s_eval calls and reports it in
  * *threads, *blocks_per_sm, *variant and its time in *best_ms (any may be
  * NULL).  Not to be called while `stream` is being captured. */
 int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream, int* threads,
@@ -337,6 +338,19 @@ int su3s_batch_add(su3s_batch* b, su3s_field* dest, const su3s_expr* e);
  * tree no persistent kernel covers are captured as separate launches in the
  * same graph.  math as for su3s_eval_math. */
 int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_sites, void* stream);
+/* Autotune and build: for every candidate launch shape (threads per block 64,
+ * 128, 256; persistent grids of at most 1, 2, 4 blocks per SM or as many as
+ * fit; tiles of 1, 2, 4 blocks' sites for the plain-load kernels) build the
+ * batch, time its graph with CUDA events on `stream` (synchronising it; the
+ * destinations are overwritten, so an item whose dest is one of its leaves
+ * changes that leaf), then leave the batch built with the fastest.  The
+ * batch may already be built (it is rebuilt).  The choice is reported in
+ * *threads, *tile_sites, *blocks_per_sm (0 = as many as fit) and its time per
+ * launch in *best_ms (any may be NULL).  Results do not depend on the launch
+ * shape.  EINVAL for a null batch, a bad arithmetic or items that overlap;
+ * not to be called while `stream` is being captured. */
+int su3s_batch_tune(su3s_batch* b, int math, void* stream, int* threads, int* tile_sites,
+                    int* blocks_per_sm, float* best_ms);
 /* Replay the graph on `stream`. */
 int su3s_batch_launch(su3s_batch* b, void* stream);
 /* Sites in the batch (sum of padded volumes times links) in *sites and the

@@ -95,6 +95,8 @@ def load(build_if_missing=False):
         "su3s_batch_create": ([PP], I),
         "su3s_batch_add": ([P, P, P], I),
         "su3s_batch_build": ([P, I, I, I, P], I),
+        "su3s_batch_tune": ([P, I, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                             ctypes.POINTER(ctypes.c_float)], I),
         "su3s_batch_launch": ([P, P], I),
         "su3s_batch_info": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64)], I),
         "su3s_batch_destroy": ([P], I),
@@ -520,6 +522,14 @@ class Batch:
 
     def build(self, math=MATH_DEFAULT, threads=0, tile_sites=0, stream=None):
         _check(_lib.su3s_batch_build(self._h, math, threads, tile_sites, _stream(stream)))
+
+    def tune(self, math=MATH_DEFAULT, stream=None):
+        """Build with the fastest launch shape (destinations are overwritten);
+        returns (threads, tile_sites, blocks_per_sm, ms per launch)."""
+        th, tile, bps, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(_lib.su3s_batch_tune(self._h, math, _stream(stream), ctypes.byref(th),
+                                    ctypes.byref(tile), ctypes.byref(bps), ctypes.byref(ms)))
+        return th.value, tile.value, bps.value, ms.value
 
     def launch(self, stream=None):
         _check(_lib.su3s_batch_launch(self._h, _stream(stream)))

@@ -192,6 +192,7 @@ struct su3s_batch {
   BTile* d_tiles = nullptr;
   BWTile* d_wtiles = nullptr;   // 32-site tiles of the staged items
   int64_t ntiles = 0, nsites = 0;
+  int64_t nplain = 0;   // tiles of the plain-load kernels (the tile size matters only for these)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -213,6 +214,7 @@ static void batch_release(su3s_batch* b) {
   b->d_items = nullptr;
   b->d_tiles = nullptr;
   b->d_wtiles = nullptr;
+  b->built = false;
 }
 
 SU3S_EXPORT int su3s_batch_create(su3s_batch** out) {
@@ -239,20 +241,8 @@ SU3S_EXPORT int su3s_batch_add(su3s_batch* b, su3s_field* dest, const su3s_expr*
   return SU3S_OK;
 }
 
-SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_sites,
-                                 void* stream) {
-  if (!b) return fail(SU3S_EINVAL, "null batch");
-  if (b->built) return fail(SU3S_EINVAL, "batch is already built");
-  if (threads == 0) threads = 256;
-  if (threads < 32 || threads > 256 || threads % 32)
-    return fail(SU3S_EINVAL, "threads per block must be a multiple of 32 in 32..256");
-  if (tile_sites == 0) tile_sites = 2 * threads;
-  if (tile_sites < threads) return fail(SU3S_EINVAL, "tile smaller than a block");
-  if (!valid_math(math))
-    return fail(SU3S_EINVAL, "bad arithmetic %d", math);
-  int m = resolve_math(SU3S_F64, math);
-  (void)stream;
-  // items run concurrently: no item may write memory another item reads or writes
+// Items run concurrently: no item may write memory another item reads or writes.
+static int check_independent(const su3s_batch* b) {
   for (size_t i = 0; i < b->items.size(); ++i) {
     const su3s_field* di = b->items[i].dest;
     for (size_t j = 0; j < b->items.size(); ++j) {
@@ -266,7 +256,13 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
         return fail(SU3S_EINVAL, "batch item %zu writes memory that item %zu reads or writes", i, j);
     }
   }
+  return SU3S_OK;
+}
 
+// Tables, grids and graph of batch b (arguments checked by the caller);
+// blocks_per_sm caps the persistent grids (0: as many as fit).
+static int batch_build(su3s_batch* b, int math, int threads, int tile_sites, int blocks_per_sm) {
+  const int m = resolve_math(SU3S_F64, math);
   std::vector<BItem> hitems;
   std::vector<BTile> by_tree[kNumBatchTrees];     // plain-load tiles
   std::vector<BWTile> staged_by_tree[kNumBatchTrees];  // 32-site tiles of staged items
@@ -319,6 +315,7 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
   }
   b->nsites = nsites;
   b->ntiles = (int64_t)htiles.size() + (int64_t)hwtiles.size();
+  b->nplain = (int64_t)htiles.size();
 
   cudaError_t ce;
   if (!hitems.empty()) {
@@ -361,6 +358,7 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
       batch_release(b);
       return cuda_fail(ce, "staged batch kernel setup");
     }
+    if (blocks_per_sm > 0 && per_sm > blocks_per_sm) per_sm = blocks_per_sm;
     if (per_sm < 1) per_sm = 1;
     const int64_t warps = (int64_t)per_sm * sm_count() * (threads / 32);
     int64_t blocks = (int64_t)per_sm * sm_count();
@@ -374,6 +372,7 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     int per_sm = 1;
     if (count[t] > 0)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(m, t), threads, 0);
+    if (blocks_per_sm > 0 && per_sm > blocks_per_sm) per_sm = blocks_per_sm;
     if (per_sm < 1) per_sm = 1;
     grid[t] = (int64_t)per_sm * sm_count();
     if (grid[t] > count[t]) grid[t] = count[t];
@@ -434,6 +433,93 @@ SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_
     return rc;
   }
   b->built = true;
+  return SU3S_OK;
+}
+
+static int check_build_args(int math, int threads, int tile_sites) {
+  if (threads < 32 || threads > 256 || threads % 32)
+    return fail(SU3S_EINVAL, "threads per block must be a multiple of 32 in 32..256");
+  if (tile_sites < threads) return fail(SU3S_EINVAL, "tile smaller than a block");
+  if (!valid_math(math)) return fail(SU3S_EINVAL, "bad arithmetic %d", math);
+  return SU3S_OK;
+}
+
+SU3S_EXPORT int su3s_batch_build(su3s_batch* b, int math, int threads, int tile_sites,
+                                 void* stream) {
+  if (!b) return fail(SU3S_EINVAL, "null batch");
+  if (b->built) return fail(SU3S_EINVAL, "batch is already built");
+  if (threads == 0) threads = 256;
+  if (tile_sites == 0) tile_sites = 2 * threads;
+  int rc = check_build_args(math, threads, tile_sites);
+  if (!rc) rc = check_independent(b);
+  if (rc) return rc;
+  (void)stream;
+  return batch_build(b, math, threads, tile_sites, 0);
+}
+
+SU3S_EXPORT int su3s_batch_tune(su3s_batch* b, int math, void* stream, int* threads_out,
+                                int* tile_sites_out, int* bps_out, float* best_ms) {
+  if (!b) return fail(SU3S_EINVAL, "null batch");
+  int rc = check_build_args(math, 256, 512);
+  if (!rc) rc = check_independent(b);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(SU3S_ECUDA, "event creation failed");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(SU3S_ECUDA, "event creation failed");
+  }
+  const int th_c[] = {64, 128, 256};
+  const int bps_c[] = {0, 1, 2, 4};
+  const int tile_c[] = {2, 1, 4};   // tile = multiple of the block (plain-load tiles only)
+  float best = 1e30f;
+  int bt = 256, btile = 512, bb = 0;
+  bool plain = true;   // known after the first build
+  for (int th : th_c) {
+    for (int bps : bps_c) {
+      for (int tm : tile_c) {
+        if (!plain && tm != 2) continue;
+        batch_release(b);
+        rc = batch_build(b, math, th, tm * th, bps);
+        if (rc) break;
+        plain = b->nplain > 0;
+        cudaError_t ce = cudaGraphLaunch(b->exec, st);   // warm-up
+        float ms = 1e30f;
+        for (int trial = 0; trial < 2 && ce == cudaSuccess; ++trial) {
+          ce = cudaEventRecord(e0, st);
+          for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(b->exec, st);
+          if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+          if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+          float t = 0.f;
+          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+          if (ce == cudaSuccess && t / 3.f < ms) ms = t / 3.f;
+        }
+        if (ce != cudaSuccess) {
+          rc = cuda_fail(ce, "batch tuning launch");
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          bt = th;
+          btile = tm * th;
+          bb = bps;
+        }
+      }
+      if (rc) break;
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  batch_release(b);
+  if (rc) return rc;
+  rc = batch_build(b, math, bt, btile, bb);
+  if (rc) return rc;
+  if (threads_out) *threads_out = bt;
+  if (tile_sites_out) *tile_sites_out = btile;
+  if (bps_out) *bps_out = bb;
+  if (best_ms) *best_ms = best;
   return SU3S_OK;
 }
 

@@ -319,6 +319,10 @@ def test_batch_rejects_items_that_touch_each_other(L):
     assert L.su3s_batch_add(b, f[4], p23) == 0       # ... which item 1 reads
     assert L.su3s_batch_build(b, 0, 0, 0, None) == 1
     assert b"item" in L.su3s_last_error()
+    assert L.su3s_batch_tune(b, 0, None, None, None, None, None) == 1
+    assert b"item" in L.su3s_last_error()
+    assert L.su3s_batch_tune(b, 9, None, None, None, None, None) == 1
+    assert L.su3s_batch_tune(None, 0, None, None, None, None, None) == 1
     assert L.su3s_batch_destroy(b) == 0
 
 

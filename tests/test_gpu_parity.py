@@ -578,6 +578,38 @@ def test_batch_matches_separate_evaluations(su3s, math):
     assert sites > 0 and tiles > 0
 
 
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
+def test_batch_tune_keeps_results(su3s, math):
+    """The batch autotuner rebuilds the graph in other launch shapes; the
+    results of the tuned batch are the same bits as the default build's."""
+    seed = synth.SEED_BASE + 4
+    shapes = config4_volumes(seed, 6)
+    b = su3s.Batch()
+    outs = []
+    for i, dims in enumerate(shapes):
+        lat = su3s.Lattice(dims)
+        v = synth.volume(dims)
+        host = {n: synth.su3(seed + 1000 * i, synth.FIELD[n], v) for n in "abcd"}
+        lay = (1, 4) if i == 0 else (0, 0)          # one item on the plain-load kernels
+        F = {n: upload(su3s, lat, host[n], layout=lay[0], block=lay[1]) for n in "abcd"}
+        z = F["a"].like()
+        b.add(z, F["a"] * F["b"] + F["c"] * F["d"])
+        outs.append((F, z))
+    b.build(math)
+    b.launch()
+    torch.cuda.synchronize()
+    ref = [z.download() for _, z in outs]
+    th, tile, bps, ms = b.tune(math)
+    assert th in (64, 128, 256) and tile in (th, 2 * th, 4 * th) and bps in (0, 1, 2, 4) and ms > 0
+    for _, z in outs:
+        z.tensor.zero_()
+    b.launch()
+    torch.cuda.synchronize()
+    for r, (_, z) in zip(ref, outs):
+        assert np.array_equal(z.download(), r)
+    assert su3s.device_error() == 0
+
+
 # --------------------------------------------- staged vs plain data movement
 @pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 @pytest.mark.parametrize("lay", [LAYOUTS[0], LAYOUTS[2], LAYOUTS[3]], ids=layout_id)
