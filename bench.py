@@ -633,8 +633,36 @@ def run_studies(su3s, synth, torch, stream, which):
                 ms = _time_ms(torch, stream, lambda: su3s.evaluate(dest, e, 0, stream))
                 res[name] = {"ms": round(ms, 5), "GB_s": round(bps * v / ms / 1e6, 1),
                              "Gsites_s": round(v / ms / 1e6, 3)}
+            # lattices whose fields fit the L2 cache: also time a rotation over
+            # enough independent copies of the fields (each evaluation reads
+            # the next copy) that their total exceeds twice the L2 size, so
+            # every evaluation reads HBM
+            rot = {}
+            ha, hb, hx = synth.su3(SEED, 0, v), synth.su3(SEED, 1, v), synth.gauss_vector(SEED, 4, v)
+            hla, hlb = synth.su3(SEED, 0, 4 * v), synth.su3(SEED, 1, 4 * v)
+            for name, bps, mk in (
+                    ("A2", B_MM, lambda: (fld(lat, MAT, 1, F64, ha), fld(lat, MAT, 1, F64, hb))),
+                    ("A3", B_MV, lambda: (fld(lat, MAT, 1, F64, ha), fld(lat, VEC, 1, F64, hx))),
+                    ("A4", 4 * B_MM, lambda: (fld(lat, MAT, 4, F64, hla), fld(lat, MAT, 4, F64, hlb)))):
+                set_bytes = bps * v
+                if set_bytes >= 2 * 129e6:
+                    continue
+                nrot = min(256, int(np.ceil(2.4 * 129e6 / set_bytes)))
+                sets = []
+                for _ in range(nrot):
+                    p, q = mk()
+                    sets.append((p.like() if name != "A3" else q.like(), p * q, p, q))
+
+                def run_all(sets=sets):
+                    for dest, e, _, _ in sets:
+                        su3s.evaluate(dest, e, 0, stream)
+                ms = _time_ms(torch, stream, run_all, reps=5, warm=2) / nrot
+                rot[name] = {"ms": round(ms, 5), "GB_s": round(bps * v / ms / 1e6, 1),
+                             "Gsites_s": round(v / ms / 1e6, 3), "copies": nrot}
+                del sets
             out.append({"study": "volume sweep", "L": L, "sites": v,
-                        "l2_resident": (3 * 144 * v) < 129e6, **res})
+                        "l2_resident": (3 * 144 * v) < 129e6, **res,
+                        **({"rotating": rot} if rot else {})})
             del a, b, x, la, lb, z, zv, zl
             torch.cuda.empty_cache()
 
