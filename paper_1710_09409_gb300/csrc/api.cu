@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -33,7 +34,7 @@ static int* device_error_ptr() {
 }
 
 // -1: choose per launch (TMA-staged where the layout allows), 0: plain loads, 1: TMA-staged
-static int g_pipeline_pref = -1;
+static std::atomic<int> g_pipeline_pref{-1};
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
@@ -182,13 +183,14 @@ static int staged_occupancy(const void* kernel, int threads, int warp_bytes) {
 }
 
 int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* out) {
-  Geo g{0, 0, g_pipeline_pref};
+  const int pref = g_pipeline_pref.load(std::memory_order_relaxed);
+  Geo g{0, 0, pref};
   const bool set = find_geometry(e->kernel[0], nvec, nmu, &g);
   if (!set) {
     // the tree's default launch; a pipeline preference overrides its variant
     g.threads = e->default_threads;
     g.bps = e->default_bps;
-    if (g_pipeline_pref >= 0 && g_pipeline_pref != e->default_variant) {
+    if (pref >= 0 && pref != e->default_variant) {
       g.threads = 0;
       g.bps = 0;
     }
@@ -471,7 +473,7 @@ int canonicalize(const su3s_expr* e, Canon* out) {
   return SU3S_OK;
 }
 
-static int g_default_math = SU3S_MATH_DF32;
+static std::atomic<int> g_default_math{SU3S_MATH_DF32};
 
 bool valid_math(int math) {
   return math == SU3S_MATH_DEFAULT || math == SU3S_MATH_F64 || math == SU3S_MATH_DF32 ||
@@ -481,7 +483,7 @@ bool valid_math(int math) {
 // Internal arithmetic id for a storage precision and a requested SU3S_MATH_*.
 int resolve_math(int prec, int math) {
   if (prec == SU3S_F64 || prec == SU3S_F64_C12) {
-    int m = math == SU3S_MATH_DEFAULT ? g_default_math : math;
+    int m = math == SU3S_MATH_DEFAULT ? g_default_math.load(std::memory_order_relaxed) : math;
     return m == SU3S_MATH_F64 ? MATH_F64 : m == SU3S_MATH_FX ? MATH_FX : MATH_DF;
   }
   return MATH_F32;
@@ -845,7 +847,7 @@ SU3S_EXPORT int su3s_eval_math(su3s_field* dest, const su3s_expr* e, int math, v
 SU3S_EXPORT int su3s_set_default_math(int math) {
   if (math == SU3S_MATH_DEFAULT || !valid_math(math))
     return fail(SU3S_EINVAL, "default arithmetic must be SU3S_MATH_F64, SU3S_MATH_DF32 or SU3S_MATH_FX");
-  g_default_math = math;
+  g_default_math.store(math, std::memory_order_relaxed);
   return ok();
 }
 
@@ -875,7 +877,7 @@ SU3S_EXPORT int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int 
   const EvalEntry* ent = find_eval(c.sig, dest->prec, math_for(dest->prec, math));
   if (!ent) return fail(SU3S_EUNSUPPORTED, "no compiled kernel for %s", c.sig.c_str());
   set_geometry(ent->kernel[0], dest->Vpad / ent->vps, dest->nmu, threads, blocks_per_sm,
-               g_pipeline_pref);
+               g_pipeline_pref.load(std::memory_order_relaxed));
   return ok();
 }
 
@@ -957,7 +959,7 @@ SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* 
 
 SU3S_EXPORT int su3s_set_pipeline(int mode) {
   if (mode < -1 || mode > 3) return fail(SU3S_EINVAL, "pipeline mode must be -1, 0, 1, 2 or 3");
-  g_pipeline_pref = mode;
+  g_pipeline_pref.store(mode, std::memory_order_relaxed);
   return ok();
 }
 
