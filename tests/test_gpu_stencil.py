@@ -9,6 +9,7 @@ colour part of the Dslash hopping term) against the CPU oracle.
 """
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import synth
@@ -95,3 +96,28 @@ def test_hop_is_hermitian_on_gpu(su3s):
     rhs = np.vdot(cplx(Ha.download()), cplx(b.download()))
     assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
     assert su3s.device_error() == 0
+
+
+@pytest.mark.parametrize("kind", ["vector", "matrix"])
+def test_hop_full_size_48(su3s, kind):
+    """The 48^4 lattice the stencil study times (default arithmetic), against
+    the oracle's hopping term over the whole lattice, on sampled sites and the
+    first and last site."""
+    dims = (48, 48, 48, 48)
+    lat = su3s.Lattice(dims)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 1, 4 * v)
+    x = host(kind, v, 2)
+    x = x / np.abs(x).max()
+    K = su3s.MATRIX if kind == "matrix" else su3s.VECTOR
+    U = field(su3s, lat, su3s.MATRIX, 4, su3s.F64, LAYOUTS[0], u)
+    X = field(su3s, lat, K, 1, su3s.F64, LAYOUTS[0], x)
+    Z = X.like()
+    su3s.hop(Z, U, X)
+    rng = np.random.default_rng(21)
+    idx = np.unique(np.concatenate([rng.choice(v, 3000, replace=False), [0, v - 1]]))
+    got = Z.unpack()[torch.from_numpy(idx).cuda()].cpu().numpy()
+    del U, X, Z
+    torch.cuda.empty_cache()
+    ref = oracle.hop(u, x, dims)[idx]
+    assert np.abs(got - ref).max() < 8 * TOL
