@@ -99,14 +99,16 @@ __global__ void __launch_bounds__(256) k_batch_tma(const BItem* __restrict__ ite
     fence_barrier_init();
   }
   __syncwarp();
+  BWTile T{0, 0, 0};
   if (i < end) {
-    const BWTile T = wt[i];
+    T = wt[i];
     issue_tile<Tree, P_F64, false>(lane, items[T.item].k, nullptr, nullptr, T.s0, T.mu, buf, bar);
   }
   uint32_t phase = 0;
   Ctx<M, NL, NS> ctx;
   while (i < end) {
-    const BWTile T = wt[i];
+    const int64_t in = i + 1;
+    const BWTile Tn = in < end ? wt[in] : T;   // read while this tile's copies land
     const KParams& p = items[T.item].k;
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase));
     if (!ok) {
@@ -117,16 +119,14 @@ __global__ void __launch_bounds__(256) k_batch_tma(const BItem* __restrict__ ite
     read_leaves<Tree, 0, P_F64, M>(buf, lane, ctx);
     fence_proxy_async_smem();
     __syncwarp();
-    const int64_t in = i + 1;
-    if (in < end) {
-      const BWTile Tn = wt[in];
+    if (in < end)
       issue_tile<Tree, P_F64, false>(lane, items[Tn.item].k, nullptr, nullptr, Tn.s0, Tn.mu, buf, bar);
-    }
 #pragma unroll
     for (int k = 0; k < (NS > 0 ? NS : 1); ++k) ctx.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
     typename M::A acc[1][W];
     acc_into<Tree, M, true, 1>(ctx, acc[0]);
     store_obj<Tree::kind, P_F64, M, 1, W>(p.dst, T.s0 + lane, T.mu, acc);
+    T = Tn;
     i = in;
   }
 }
