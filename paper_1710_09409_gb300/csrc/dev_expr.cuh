@@ -225,33 +225,33 @@ __device__ __forceinline__ void mm_acc(typename M::A* z, const typename M::R* x,
           M::template fma<false, -SG * sx * sy>(re, x[2 * xi + 1], y[2 * yi + 1]);
           M::template fma<false, SG * sx>(im, x[2 * xi + 1], y[2 * yi]);
         }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      typename M::A& re = z[2 * (3 * i + k)];
-      typename M::A& im = z[2 * (3 * i + k) + 1];
+      for (int k = 0; k < 3; ++k) {
+        typename M::A& re = z[2 * (3 * i + k)];
+        typename M::A& im = z[2 * (3 * i + k) + 1];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int xi = AX ? (3 * j + i) : (3 * i + j);
-        const int yi = AY ? (3 * k + j) : (3 * j + k);
-        const typename M::R& xr = x[2 * xi];
-        const typename M::R& xm = x[2 * xi + 1];
-        const typename M::R& yr = y[2 * yi];
-        const typename M::R& ym = y[2 * yi + 1];
-        if (FIRST && j == 0) {
-          M::template fma<true, SG>(re, xr, yr);
-          M::template fma<true, SG * sy>(im, xr, ym);
-        } else {
-          M::template fma<false, SG>(re, xr, yr);
-          M::template fma<false, SG * sy>(im, xr, ym);
+        for (int j = 0; j < 3; ++j) {
+          const int xi = AX ? (3 * j + i) : (3 * i + j);
+          const int yi = AY ? (3 * k + j) : (3 * j + k);
+          const typename M::R& xr = x[2 * xi];
+          const typename M::R& xm = x[2 * xi + 1];
+          const typename M::R& yr = y[2 * yi];
+          const typename M::R& ym = y[2 * yi + 1];
+          if (FIRST && j == 0) {
+            M::template fma<true, SG>(re, xr, yr);
+            M::template fma<true, SG * sy>(im, xr, ym);
+          } else {
+            M::template fma<false, SG>(re, xr, yr);
+            M::template fma<false, SG * sy>(im, xr, ym);
+          }
+          M::template fma<false, -SG * sx * sy>(re, xm, ym);
+          M::template fma<false, SG * sx>(im, xm, yr);
         }
-        M::template fma<false, -SG * sx * sy>(re, xm, ym);
-        M::template fma<false, SG * sx>(im, xm, yr);
       }
-    }
+  }
 }
 
 // z (+)= SG * op(x) * v, x 3x3, v 3-vector.
