@@ -259,9 +259,15 @@ struct MathFX {
   // Raw FP64 bits of W reals -> shared-exponent fixed point.
   template <int W>
   __device__ static __forceinline__ void normalize_obj(R* x) {
-    uint32_t amax = 0;
+    // largest magnitude by a pairwise tree (depth log2 W, not a W-long chain)
+    uint32_t m[W];
 #pragma unroll
-    for (int i = 0; i < W; ++i) amax = max(amax, (uint32_t)x[i].h & 0x7FFFFFFFu);
+    for (int i = 0; i < W; ++i) m[i] = (uint32_t)x[i].h & 0x7FFFFFFFu;
+#pragma unroll
+    for (int w = 1; w < W; w *= 2)
+#pragma unroll
+      for (int i = 0; i + w < W; i += 2 * w) m[i] = max(m[i], m[i + w]);
+    const uint32_t amax = m[0];
     const int E = max((int)(amax >> 20), kFxEmin);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
@@ -280,16 +286,27 @@ struct MathFX {
   // W accumulators (scales may differ) -> one object with a shared exponent.
   template <int W>
   __device__ static __forceinline__ void finish_obj(R* out, const A* a) {
-    int e = a[0].e;
+    // largest scale and the OR of the magnitudes by pairwise trees
+    int es[W];
 #pragma unroll
-    for (int i = 1; i < W; ++i) e = max(e, a[i].e);
+    for (int i = 0; i < W; ++i) es[i] = a[i].e;
+#pragma unroll
+    for (int w = 1; w < W; w *= 2)
+#pragma unroll
+      for (int i = 0; i + w < W; i += 2 * w) es[i] = max(es[i], es[i + w]);
+    const int e = es[0];
     long long T[W];
-    uint64_t orv = 0;
+    uint64_t ov[W];
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       T[i] = fx_sar(fx_total(a[i]), (uint32_t)(e - a[i].e));
-      orv |= (uint64_t)(T[i] ^ (T[i] >> 63));
+      ov[i] = (uint64_t)(T[i] ^ (T[i] >> 63));
     }
+#pragma unroll
+    for (int w = 1; w < W; w *= 2)
+#pragma unroll
+      for (int i = 0; i + w < W; i += 2 * w) ov[i] |= ov[i + w];
+    const uint64_t orv = ov[0];
     const int sh = max(64 - __clzll((long long)orv) - 53, 0);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
