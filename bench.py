@@ -953,15 +953,16 @@ def main():
     bytes_step = sum(r.nbytes for r in rows)
     value = aggregate_gbs(bytes_step, ws, ms_step)
 
+    peak, peak_kind = read_peaks()
     row_out = []
     for r, ms in zip(rows, per_row):
         m = float(np.mean(ms))
+        gbs = r.nbytes / (m * 1e-3) / 1e9
         row_out.append({"row": r.name, "storage": r.dtype,
                         "arith": MATH_DTYPE[args.math] if r.dtype.startswith("f64") else "f32",
-                        "ms": round(m, 5),
-                        "GB_s": round(r.nbytes / (m * 1e-3) / 1e9, 1),
+                        "ms": round(m, 5), "GB_s": round(gbs, 1),
+                        "frac_of_peak": round(gbs / peak, 4),
                         "Gsites_s": round(r.sites / (m * 1e-3) / 1e9, 3)})
-    peak, peak_kind = read_peaks()
     # dominant kernel: the largest share of the step time
     di = int(np.argmax([np.mean(ms) for ms in per_row]))
     dm = float(np.mean(per_row[di]))
