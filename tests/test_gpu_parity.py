@@ -782,6 +782,7 @@ def test_largest_soa_fields(su3s, dims):
     against the oracle."""
     v = synth.volume(dims)
     need = v * (144 + 48)
+    torch.cuda.empty_cache()          # memory cached by earlier tests counts as used
     if torch.cuda.mem_get_info()[0] < need + (4 << 30):
         pytest.skip("needs %.0f GB of free device memory" % (need / 1e9))
     lat = su3s.Lattice(dims)
