@@ -321,7 +321,10 @@ int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* stream, int*
 
 /* ------------------------------------------------------------------------
  * Batching: many (dest, expr) pairs of uneven volumes in one persistent
- * launch, captured in a CUDA graph
+ * launch, captured in a CUDA graph.  Each item is the one-pass evaluation of
+ * Sec. 3, Listing 1 (_odata[ss] = eval(ss, expr)) on its own lattice; the
+ * paper evaluates one lattice per launch and has no batching, which is a
+ * service of this library.
  * ---------------------------------------------------------------------- */
 
 int su3s_batch_create(su3s_batch** out);
@@ -359,7 +362,9 @@ int su3s_batch_info(const su3s_batch* b, int64_t* sites, int64_t* tiles);
 int su3s_batch_destroy(su3s_batch* b);
 
 /* ------------------------------------------------------------------------
- * Differentiation
+ * Differentiation: the reverse mode of the evaluation of Sec. 3, Listing 1
+ * (the paper has no counterpart; for z = x*y of Sec. 4, Listing 3 it gives
+ * dX = dZ Y^dagger, dY = X^dagger dZ)
  * ---------------------------------------------------------------------- */
 
 /* Reverse mode through `e` for a real loss L whose gradient with respect to
@@ -386,7 +391,9 @@ int su3s_tune_adjoint(const su3s_expr* e, const su3s_field* grad_out, su3s_field
 int su3s_expr_num_leaves(const su3s_expr* e, int* n);
 
 /* ------------------------------------------------------------------------
- * Reductions and projections
+ * Reductions and projections (no counterpart in the paper: the loss of the
+ * reverse mode, and the FP64 projection to SU(3) of fields kept in reduced
+ * precision)
  * ---------------------------------------------------------------------- */
 
 /* *dev_out (device memory, one double) = sum over sites, links and
