@@ -206,6 +206,16 @@ def host_mem_available():
     return None
 
 
+def e2e_host_shortage(dims, local_ranks, available):
+    """None if every rank on this node can pin its end-to-end buffers (at most
+    85% of the available host memory in all), else the reason, one line."""
+    need = e2e_host_bytes(dims) * local_ranks
+    if available is None or need <= 0.85 * available:
+        return None
+    return ("host memory: %d ranks need %.0f GB pinned, %.0f GB available"
+            % (local_ranks, need / 1e9, available / 1e9))
+
+
 def build_rows(su3s, synth, torch, with_host, dims=DIMS, want=lambda name: True):
     """Allocate fields, fill them from the seeded generator, return the rows
     whose names pass `want`."""
@@ -884,13 +894,9 @@ def main():
     with_host = not args.no_e2e
     e2e_skip = None
     if with_host:
-        # every rank on this node pins its own host buffers
-        lws = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
-        need, avail = e2e_host_bytes(dims) * lws, host_mem_available()
-        if avail is not None and need > 0.85 * avail:
-            with_host = False
-            e2e_skip = ("host memory: %d ranks need %.0f GB pinned, %.0f GB available"
-                        % (lws, need / 1e9, avail / 1e9))
+        e2e_skip = e2e_host_shortage(dims, int(os.environ.get("LOCAL_WORLD_SIZE", "1")),
+                                     host_mem_available())
+        with_host = e2e_skip is None
     rows, keep = build_rows(su3s, synth, torch, with_host, dims, want)
     torch.cuda.synchronize()
     tuned = []

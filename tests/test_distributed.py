@@ -59,3 +59,17 @@ def test_reference_arm_nonzero_rank_exits_quietly():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_e2e_host_memory_guard():
+    """Each rank pins its own end-to-end host buffers (~23 GB at 48^4); the
+    bench reports the shortage instead of failing when the node cannot hold
+    every rank's buffers."""
+    sys.path.insert(0, ROOT)
+    import bench
+    per_rank = bench.e2e_host_bytes((48, 48, 48, 48))
+    assert 20e9 < per_rank < 26e9
+    assert bench.e2e_host_shortage((48, 48, 48, 48), 1, 209e9) is None
+    assert bench.e2e_host_shortage((48, 48, 48, 48), 8, None) is None
+    msg = bench.e2e_host_shortage((48, 48, 48, 48), 8, 150e9)
+    assert msg.startswith("host memory: 8 ranks")
