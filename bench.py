@@ -936,7 +936,8 @@ def main():
         gbs = r.nbytes / (m * 1e-3) / 1e9
         row_out.append({"row": r.name, "storage": r.dtype,
                         "arith": MATH_DTYPE[args.math] if r.dtype.startswith("f64") else "f32",
-                        "ms": round(m, 5), "GB_s": round(gbs, 1),
+                        "ms": round(m, 5), "ms_median": round(float(np.median(ms)), 5),
+                        "GB_s": round(gbs, 1),
                         "frac_of_peak": round(gbs / peak, 4),
                         "Gsites_s": round(r.sites / (m * 1e-3) / 1e9, 3)})
     # dominant kernel: the largest share of the step time
