@@ -58,7 +58,7 @@ MATH_DESC = {"fx": "shared-exponent fixed-point (fx)", "df32": "pair-of-FP32 (df
              "f64": "native FP64 (f64)"}
 # arithmetic type of the rows with FP64 storage under each arithmetic
 MATH_DTYPE = {"fx": "int64", "df32": "df32", "f64": "f64"}
-MATH_ERR = {"fx": "7.8e-16 - 1.4e-15", "df32": "3.6e-14 - 5.7e-14", "f64": "3.3e-16 - 6.7e-16"}
+MATH_ERR = {"fx": "7.8e-16 - 1.6e-15", "df32": "3.6e-14 - 5.7e-14", "f64": "3.3e-16 - 6.7e-16"}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on a
 # 32^4 lattice (1,048,576 sites; the batch row: its 64 fixed lattices), from one
