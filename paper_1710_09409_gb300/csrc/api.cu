@@ -565,7 +565,7 @@ static int do_eval(su3s_field* dest, const su3s_expr* e, int math, cudaStream_t 
 // =================================================================== C ABI
 SU3S_EXPORT const char* su3s_last_error(void) { return g_err.c_str(); }
 
-SU3S_EXPORT int su3s_version(void) { return 10000; }
+SU3S_EXPORT int su3s_version(void) { return 10100; }
 
 SU3S_EXPORT int su3s_lattice_create(int lx, int ly, int lz, int lt, su3s_lattice** out) {
   if (!out) return fail(SU3S_EINVAL, "null output handle");

@@ -347,3 +347,13 @@ def test_stored_transfer_sizes_and_validation(L, kind, prec, ncomp, eb):
         assert L.su3s_field_download_stored(None, buf, n.value, None) == 1
         assert L.su3s_field_stored_bytes(h, None) == 1
         assert L.su3s_field_destroy(h) == 0
+
+
+def test_version_and_last_error(L):
+    """su3s_version is 10000*major + 100*minor + patch; a successful call leaves
+    the thread's message empty, a failed one sets it."""
+    v = L.su3s_version()
+    assert v >= 10000 and v % 100 < 100 and (v // 100) % 100 < 100
+    rc, lat = _lat(L, (2, 2, 2, 2))
+    assert rc == 0 and L.su3s_last_error() == b""
+    assert L.su3s_lattice_volume(None, None) == 1 and L.su3s_last_error() != b""
