@@ -579,6 +579,56 @@ def test_batch_matches_separate_evaluations(su3s, math):
 
 
 @pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
+def test_batch_covers_every_persistent_tree(su3s, math):
+    """One item of each tree the persistent kernels cover, on a lattice that the
+    staged kernel takes (SoA) and on one that the plain-load kernel takes
+    (4-site blocks): same bits as a separate evaluation, and the oracle's value."""
+    dims = (4, 4, 4, 6)
+    v = synth.volume(dims)
+    lat = su3s.Lattice(dims)
+    seed = synth.SEED_BASE + 9
+    host = {n: synth.su3(seed, synth.FIELD[n], v) for n in "abcd"}
+    hv = synth.gauss_vector(seed, synth.FIELD["v"], v)
+    al, be = 0.75, -1.25
+    trees = {
+        "MM": (("mul", ("leaf", "a"), ("leaf", "b")), lambda F: F["a"] * F["b"]),
+        "E1": (E1, lambda F: F["a"] * F["b"] + F["c"] * F["d"]),
+        "MV": (("mul", ("leaf", "a"), ("leaf", "v")), lambda F: F["a"] * F["v"]),
+        "E2": (E2, lambda F: F["a"] * F["b"] * F["c"] + 0.5 * F["d"]),
+        "E3": (E3, lambda F: F["a"].adj() * F["b"] - F["b"] * F["a"].adj()),
+        "MMM": (("mul", ("mul", ("leaf", "a"), ("leaf", "b")), ("leaf", "c")),
+                lambda F: F["a"] * F["b"] * F["c"]),
+        "E1Lin": (("add", ("scale", al, ("mul", ("leaf", "a"), ("leaf", "b"))),
+                   ("scale", be, ("mul", ("leaf", "c"), ("leaf", "d")))),
+                  lambda F: al * (F["a"] * F["b"]) + be * (F["c"] * F["d"])),
+        "AdjMM": (("mul", ("adj", ("leaf", "a")), ("leaf", "b")), lambda F: F["a"].adj() * F["b"]),
+    }
+    b = su3s.Batch()
+    items = []
+    for lay in ((0, 0), (1, 4)):
+        for name, (tree, mk) in trees.items():
+            # every item reads its own copies: batch items must not overlap
+            F = {n: upload(su3s, lat, host[n], layout=lay[0], block=lay[1]) for n in "abcd"}
+            F["v"] = upload(su3s, lat, hv, kind=su3s.VECTOR, layout=lay[0], block=lay[1])
+            z = (F["v"] if name == "MV" else F["a"]).like()
+            b.add(z, mk(F))
+            items.append((name, tree, mk, F, z))
+    b.build(math)
+    b.launch()
+    torch.cuda.synchronize()
+    leaves = dict(host, v=hv)
+    for name, tree, mk, F, z in items:
+        sep = z.like()
+        su3s.evaluate(sep, mk(F), math)
+        got = z.download()
+        assert np.array_equal(sep.download(), got), name
+        ref = oracle.eval_tree(tree, {n: leaves[n] for n in oracle.leaf_names(tree)})
+        scale = max(1.0, np.abs(hv).max() * 3) if name == "MV" else 1.0
+        assert np.abs(got - ref).max() < 4 * TOL * scale, name
+    assert su3s.device_error() == 0
+
+
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_batch_tune_keeps_results(su3s, math):
     """The batch autotuner rebuilds the graph in other launch shapes; the
     results of the tuned batch are the same bits as the default build's."""
