@@ -276,10 +276,11 @@ int su3s_set_default_math(int math);
 int su3s_catalogue(char* buf, size_t cap);
 
 /* Fix the launch geometry used for `e` into `dest` (threads per block
- * 32..1024, multiple of 32; blocks_per_sm 0 = one thread per site-vector,
- * else a grid-stride grid of blocks_per_sm * SMs blocks).  Results do not
- * depend on the geometry.  Applies to later su3s_eval calls with the same
- * kernel and volume. */
+ * 32..256, multiple of 32; blocks_per_sm 0..64: 0 = one thread per
+ * site-vector, else a grid-stride grid of blocks_per_sm * SMs blocks) with the
+ * data movement set by su3s_set_pipeline at this call.  Results do not depend
+ * on the geometry.  Applies to later su3s_eval calls with the same kernel and
+ * volume.  EINVAL for values out of range. */
 int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int threads,
                     int blocks_per_sm);
 

@@ -103,6 +103,29 @@ def test_lorentz_links(su3s, lay, math):
     assert np.abs(z.download() - oracle.mm(f["a"], f["b"])).max() < TOL
 
 
+@pytest.mark.parametrize("layout,block", [(0, 0), (1, 1024)], ids=["soa", "aosoa1024"])
+def test_largest_link_count_and_site_block(su3s, layout, block):
+    """The API's limits of the field shape: 8 objects per site, and the largest
+    site block (1024, more than the lattice's 630 sites: one padded block), for
+    a product, a fused tree and its reverse mode."""
+    dims = (6, 5, 7, 3)
+    v = synth.volume(dims)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED + 11, nmu=8, names=("a", "b", "c", "d", "w"))
+    F = {n: upload(su3s, lat, f[n], nmu=8, layout=layout, block=block) for n in "abcdw"}
+    z = F["a"].like()
+    su3s.evaluate(z, F["a"] * F["b"])
+    assert np.abs(z.download() - oracle.mm(f["a"], f["b"])).max() < TOL
+    su3s.evaluate(z, F["a"] * F["b"] + F["c"] * F["d"])
+    assert np.abs(z.download() - oracle.eval_tree(E1, f)).max() < 2 * TOL
+    grads = [F["a"].like() for _ in range(4)]
+    su3s.eval_adjoint(F["a"] * F["b"] + F["c"] * F["d"], F["w"], grads)
+    ref = oracle.eval_adjoint(E1, {n: f[n] for n in "abcd"}, f["w"])
+    wscale = np.abs(f["w"]).max() * 3
+    for n, g in zip("abcd", grads):
+        assert np.abs(g.download() - ref[n]).max() < TOL * wscale, n
+
+
 @pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_gaussian_operands(su3s, math):
     dims = (6, 5, 7, 3)
@@ -124,6 +147,32 @@ def test_dest_aliases_leaf(su3s):
     a, b = upload(su3s, lat, f["a"]), upload(su3s, lat, f["b"])
     su3s.evaluate(b, a * b)          # b <- a*b in place
     assert np.abs(b.download() - oracle.mm(f["a"], f["b"])).max() < TOL
+
+
+def test_dest_aliases_leaf_every_pipeline(su3s):
+    """A destination that is one of the tree's leaves, in every data-movement
+    mode, with many tiles per warp (the staged kernels fetch the next tile
+    while the current one is stored): c <- a*b + c*d, and a <- adj(a)*b - b*adj(a),
+    which reads the overwritten leaf twice."""
+    dims = (16, 16, 16, 18)          # a volume of its own: the forced launch stays here
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED + 12, names=("a", "b", "c", "d"))
+    ref1, ref3 = oracle.eval_tree(E1, f), oracle.eval_tree(E3, f)
+    try:
+        for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF, su3s.PIPE_TMA_RING):
+            su3s.set_pipeline(mode)
+            F = {n: upload(su3s, lat, f[n]) for n in "abcd"}
+            e1 = F["a"] * F["b"] + F["c"] * F["d"]
+            su3s.set_launch(F["c"], e1, 32, 1)        # 152 one-warp blocks: ~15 tiles each
+            su3s.evaluate(F["c"], e1)
+            assert np.abs(F["c"].download() - ref1).max() < 2 * TOL, mode
+            e3 = F["a"].adj() * F["b"] - F["b"] * F["a"].adj()
+            su3s.set_launch(F["a"], e3, 32, 1)
+            su3s.evaluate(F["a"], e3)
+            assert np.abs(F["a"].download() - ref3).max() < 2 * TOL, mode
+    finally:
+        su3s.set_pipeline(su3s.PIPE_AUTO)
+    assert su3s.device_error() == 0
 
 
 def test_zero_and_identity_inputs(su3s):
