@@ -271,8 +271,11 @@ int su3s_eval_math(su3s_field* dest, const su3s_expr* e, int math, void* stream)
  * other values. */
 int su3s_set_default_math(int math);
 
-/* Names of the compiled catalogue trees, one per line, into buf (truncated to
- * cap bytes, NUL-terminated). */
+/* The compiled kernels, one per line, into buf (truncated to cap bytes,
+ * NUL-terminated): "eval <signature> <storage> <arithmetic>" for the forward
+ * catalogue and "adjoint <signature> f64 <arithmetic>" for the reverse mode,
+ * storage one of f64 f32 bf16 f16 f64_c12 f32_c12 and arithmetic one of f64
+ * df32 fx (FP64 storage) or f32 (reduced storage).  EINVAL on a null buffer. */
 int su3s_catalogue(char* buf, size_t cap);
 
 /* Fix the launch geometry used for `e` into `dest` (threads per block
@@ -421,18 +424,20 @@ int su3s_reunitarize(su3s_field* dst, const su3s_field* src, void* stream);
 
 /* dst(x) = src(x + shift * e_dim) at every site, link and component: a copy
  * of the stored objects in their storage format (any kind and precision,
- * bit exact).  dst and src have the same kind, shape, precision and layout
- * and do not overlap (EINVAL).  dim in 0..3 (EINVAL otherwise); any shift,
- * taken modulo the extent.  Pad sites are not touched. */
+ * bit exact).  dst and src have the same kind (ETYPE otherwise), the same
+ * lattice, links, precision and layout (ESHAPE otherwise), and do not overlap
+ * (EINVAL).  dim in 0..3 (EINVAL otherwise); any shift, taken modulo the
+ * extent.  Pad sites are not touched. */
 int su3s_cshift(su3s_field* dst, const su3s_field* src, int dim, int shift, void* stream);
 
 /* dst(x) = sum_mu [ U_mu(x) v(x + mu) + U_mu(x - mu)^dagger v(x - mu) ]: the
  * colour part of the Wilson Dslash hopping term.  U: matrix field with 4 links
  * per site; v, dst: matrix or colour-vector fields with one object per site,
- * of the same kind; all FP64 storage on one lattice (any layouts).  Each of
- * the 8 products is accumulated on its own and the products are added in the
- * arithmetic `math` (as for su3s_eval_math).  dst overlapping U or v: EINVAL.
- * Pad sites are not touched. */
+ * of the same kind (ETYPE otherwise); all FP64 storage (EUNSUPPORTED
+ * otherwise) on one lattice (ESHAPE otherwise), in any layouts.  Each of the
+ * 8 products is accumulated on its own and the products are added in the
+ * arithmetic `math` (as for su3s_eval_math; EINVAL for another value).  dst
+ * overlapping U or v: EINVAL.  Pad sites are not touched. */
 int su3s_hop(su3s_field* dst, const su3s_field* U, const su3s_field* v, int math, void* stream);
 
 #ifdef __cplusplus
