@@ -313,6 +313,17 @@ int su3s_set_pipeline(int mode);
  * tensor copies and staged nothing (results are incomplete in both cases). */
 int su3s_device_error(int* code, void* stream);
 
+/* Diagnostic of the bounded waits (the paper has no counterpart): one warp
+ * waits, with the pipelines' bounded-wait routine cut to `polls` polls
+ * (1..2^20, EINVAL otherwise), on a staging barrier that nothing completes.
+ * The wait gives up, the kernel records code 1 in the device error word (read
+ * it with su3s_device_error) and returns; *cycles receives the SM clock
+ * cycles the wait took (-1 if it did not give up).  Nothing faults and the
+ * context stays usable.  Synchronises `stream`.  The pipelines themselves give
+ * up after 2^18 polls: a poll that finds the phase incomplete suspends the
+ * thread for ~7,800 cycles on GB300, so about one second. */
+int su3s_selftest_bounded_wait(uint32_t polls, int64_t* cycles, void* stream);
+
 /* Autotune the launch geometry for `e` into `dest`: times each candidate
  * (data movement 0..3 as for su3s_set_pipeline, threads 64..256, full or
  * grid-stride grids) with CUDA events on `stream` (synchronising it; dest is

@@ -90,6 +90,7 @@ def load(build_if_missing=False):
         "su3s_set_launch": ([P, P, I, I, I], I),
         "su3s_set_pipeline": ([I], I),
         "su3s_device_error": ([ctypes.POINTER(I), P], I),
+        "su3s_selftest_bounded_wait": ([ctypes.c_uint32, ctypes.POINTER(I64), P], I),
         "su3s_tune": ([P, P, I, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                        ctypes.POINTER(ctypes.c_float)], I),
         "su3s_batch_create": ([PP], I),
@@ -162,6 +163,15 @@ def device_error(stream=None):
 
 
 # ---------------------------------------------------------------- lattice
+def selftest_bounded_wait(polls=4096, stream=None):
+    """Run the bounded-wait diagnostic (a wait that nothing completes gives up
+    after `polls` polls); returns the SM cycles the wait took.  The device
+    error word is left at 1 (read it with device_error())."""
+    c = ctypes.c_int64()
+    _check(load().su3s_selftest_bounded_wait(polls, ctypes.byref(c), _stream(stream)))
+    return c.value
+
+
 class Lattice:
     """A 4-d lattice Lx*Ly*Lz*Lt (site index x + Lx*(y + Ly*(z + Lz*t)))."""
 

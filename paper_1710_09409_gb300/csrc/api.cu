@@ -976,6 +976,46 @@ SU3S_EXPORT int su3s_device_error(int* code, void* stream) {
   return ok();
 }
 
+// One warp waits on a staging barrier that nothing completes (no copy is
+// issued and nothing arrives), with the pipelines' bounded wait cut to `polls`
+// polls: the wait gives up, the kernel records the time-out code in the device
+// error word as a pipeline would, writes the SM cycles the wait took, and
+// returns.
+__global__ void k_selftest_wait(int* err, uint32_t polls, long long* cycles) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const long long t0 = clock64();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_polls(&bar, 0, polls));
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) {
+    if (!ok && err) atomicExch(err, kErrTmaTimeout);
+    *cycles = ok ? -1 : t1 - t0;
+  }
+}
+
+SU3S_EXPORT int su3s_selftest_bounded_wait(uint32_t polls, int64_t* cycles, void* stream) {
+  if (!cycles) return fail(SU3S_EINVAL, "null argument");
+  if (polls < 1 || polls > (1u << 20)) return fail(SU3S_EINVAL, "polls must be 1..2^20");
+  cudaStream_t st = (cudaStream_t)stream;
+  void* d = nullptr;
+  cudaError_t e = scratch_alloc(&d, sizeof(long long), st);
+  if (e != cudaSuccess) return fail(SU3S_ENOMEM, "scratch: %s", cudaGetErrorString(e));
+  k_selftest_wait<<<1, 32, 0, st>>>(device_error_ptr(), polls, (long long*)d);
+  e = cudaGetLastError();
+  long long c = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c, d, sizeof c, cudaMemcpyDeviceToHost, st);
+  cudaError_t e2 = scratch_free(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "bounded-wait self-test scratch");
+  *cycles = c;
+  return ok();
+}
+
 // ---------------------------------------------------------------- adjoint
 // Checks and kernel parameters of a reverse-mode evaluation.
 static int prepare_adjoint(const su3s_expr* e, const su3s_field* gout, su3s_field* const* gleaves,

@@ -18,7 +18,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 }
 __device__ __forceinline__ uint32_t smem_u32_base(const void* p) { return smem_u32(p); }
 
-constexpr uint32_t kTmaSpinLimit = 1u << 24;
+// A poll that finds the phase incomplete suspends the thread for ~7,800 SM
+// cycles (measured with su3s_selftest_bounded_wait on GB300: ~3.8 us), so
+// 2^18 polls give up after about one second, a million times the latency of a
+// tile's copies.
+constexpr uint32_t kTmaSpinLimit = 1u << 18;
 constexpr int kErrTmaTimeout = 1;
 constexpr int kErrSmemAlign = 2;   // dynamic shared memory not 128-byte aligned: nothing staged
 
@@ -87,11 +91,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kTmaSpinLimit; ++i)
+// Wait for the phase with the given parity for at most `polls` polls; false
+// on time-out.
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Bounded wait of the pipelines (kTmaSpinLimit polls); false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_polls(bar, parity, kTmaSpinLimit);
 }
 
 __device__ __forceinline__ void report_timeout(int* err, uint64_t* bar, uint32_t parity) {

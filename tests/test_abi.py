@@ -357,3 +357,10 @@ def test_version_and_last_error(L):
     rc, lat = _lat(L, (2, 2, 2, 2))
     assert rc == 0 and L.su3s_last_error() == b""
     assert L.su3s_lattice_volume(None, None) == 1 and L.su3s_last_error() != b""
+
+
+def test_bounded_wait_selftest_validation(L):
+    c = ctypes.c_int64()
+    assert L.su3s_selftest_bounded_wait(0, ctypes.byref(c), None) == 1
+    assert L.su3s_selftest_bounded_wait((1 << 20) + 1, ctypes.byref(c), None) == 1
+    assert L.su3s_selftest_bounded_wait(16, None, None) == 1

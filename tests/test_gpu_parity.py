@@ -843,6 +843,32 @@ def test_reunitarize(su3s, prec, fmt, tol):
     assert np.abs(u @ np.conj(np.swapaxes(u, 1, 2)) - np.eye(3)).max() < max(tol, 1e-13) * 10
 
 
+# ------------------------------------------------------ failure detection
+def test_bounded_wait_gives_up_and_context_survives(su3s):
+    """A staging wait that nothing completes (no copy issued, nothing arrives)
+    gives up after its poll limit, records code 1 in the device error word, and
+    the kernel returns: the context stays usable and the next evaluation is
+    right.  The measured time per poll gives the pipelines' give-up time."""
+    import json
+    assert su3s.device_error() == 0
+    polls = 4096
+    cycles = su3s.selftest_bounded_wait(polls)
+    assert cycles > 0
+    assert su3s.device_error() == 1
+    assert su3s.device_error() == 0          # the read cleared it
+    dims = (3, 2, 1, 5)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED)
+    a, b = upload(su3s, lat, f["a"]), upload(su3s, lat, f["b"])
+    z = a.like()
+    su3s.evaluate(z, a * b)
+    assert np.abs(z.download() - oracle.mm(f["a"], f["b"])).max() < TOL
+    assert su3s.device_error() == 0
+    print(json.dumps({"bounded_wait_polls": polls, "cycles": cycles,
+                      "cycles_per_poll": cycles / polls,
+                      "pipeline_give_up_cycles": cycles / polls * (1 << 18)}))
+
+
 # ------------------------------------------------------ full-size sampling
 @pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_full_size_48_sampled(su3s, math):
