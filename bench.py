@@ -730,6 +730,31 @@ def run_studies(su3s, synth, torch, stream, which):
                 del a, b, z
             torch.cuda.empty_cache()
 
+    if "interp" in which:
+        # trees outside the compiled catalogue run the uniform interpreter
+        # kernel (registers in local memory); beside them a catalogue tree of
+        # the same byte count for comparison
+        dims = (48, 48, 48, 48)
+        v = synth.volume(dims)
+        lat = su3s.Lattice(dims)
+        F = {n: fld(lat, MAT, 1, F64, synth.su3(SEED + 7, i, v)) for i, n in enumerate("abcd")}
+        a, b, c, d = (F[n] for n in "abcd")
+        z = a.like()
+        cat = {sig for (_, sig, p, m) in su3s.catalogue()}
+        for name, e, bsite in (("(a+b)*adj(c)", (a + b) * c.adj(), 4 * 144),
+                               ("a*b+c*d (catalogue)", a * b + c * d, 5 * 144),
+                               ("a*(b+c)-d", a * (b + c) - d, 5 * 144),
+                               ("adj(a*b)*c", (a * b).adj() * c, 4 * 144)):
+            for mname in MATH_NAMES:
+                ms = _time_ms(torch, stream,
+                              lambda: su3s.evaluate(z, e, MATH_IDS[mname], stream))
+                out.append({"study": "interpreter", "tree": name, "math": mname,
+                            "compiled": e.signature() in cat, "lattice": list(dims),
+                            "ms": round(ms, 5), "B_per_site": bsite,
+                            "GB_s": round(bsite * v / ms / 1e6, 1)})
+        del F, a, b, c, d, z
+        torch.cuda.empty_cache()
+
     if "stencil" in which:
         # nearest-neighbour operations (Sec. 7): the hopping term and the Cshift;
         # algorithmic bytes: every input object once, the output once
@@ -832,7 +857,7 @@ def main():
     ap.add_argument("--dims", default="48,48,48,48", help="lattice extents (default 48^4)")
     ap.add_argument("--study", default="",
                     help="comma list of studies to run instead of the step: volume, fused, "
-                         "precision, batch, layout, stencil (one JSON line each)")
+                         "precision, batch, layout, stencil, interp (one JSON line each)")
     ap.add_argument("--math", default="df32", choices=["fx", "df32", "f64"],
                     help="arithmetic of the FP64-storage rows in the step (the others are "
                          "timed beside it)")
