@@ -2,8 +2,13 @@
 // catalogue (FP64 storage).  The tree is flattened on the host into a short
 // register program; every thread runs the same program on its own site, so
 // control flow is uniform across the grid (no divergence), and the whole tree
-// is still evaluated in one read/write pass (Sec. 3, Listing 1).  Registers
-// live in per-thread local memory.
+// is still evaluated in one read/write pass (Sec. 3, Listing 1).  The register
+// file lives in shared memory, laid out [register][real][thread] so that
+// consecutive threads touch consecutive words; an instruction copies its
+// operands into fixed-size arrays (their widths are known per operation), so
+// the arithmetic runs on registers, and writes its result back.  The host
+// sizes the shared memory to the registers the program uses: leaves are
+// loaded at their first use and every register is freed after its last.
 #include <string.h>
 
 #include <vector>
@@ -29,99 +34,176 @@ struct IProg {
   int32_t n;
   int32_t root;
   int32_t root_kind;
-  int32_t pad;
+  int32_t nregs;   // registers the program uses (shared memory is sized to them)
   IIns ins[kIMax];
 };
 
+// The register file: real r of register g of this thread.
 template <class M>
-__device__ __forceinline__ void i_load(const FieldDesc& f, int kind, int64_t s, int mu,
-                                       typename M::R* r) {
+struct IRegs {
+  typename M::R* base;
+  int nt, tid;
+  __device__ __forceinline__ typename M::R& at(int g, int r) const {
+    return base[(g * 18 + r) * nt + tid];
+  }
+  template <int W>
+  __device__ __forceinline__ void get(int g, typename M::R* v) const {
+#pragma unroll
+    for (int r = 0; r < W; ++r) v[r] = at(g, r);
+  }
+  template <int W>
+  __device__ __forceinline__ void put(int g, const typename M::R* v) const {
+#pragma unroll
+    for (int r = 0; r < W; ++r) at(g, r) = v[r];
+  }
+};
+
+// Object of W reals of field f (FP64 storage) at site s, link mu.
+template <class M, int W>
+__device__ __forceinline__ void i_load(const FieldDesc& f, int64_t s, int mu, typename M::R* r) {
   const int64_t b = elem_base(f, s, mu);
-  if (kind == KR) {
+  if constexpr (W == 1) {
     r[0] = StoreReal::template load<M>(f.ptr, b);
-    M::template normalize_obj<1>(r);
-    return;
-  }
-  const int nc = kind == KM ? 9 : 3;
-  for (int c = 0; c < nc; ++c) {
-    typename M::R re[1], im[1];
-    Store<P_F64>::template load<M>(f.ptr, b + c * f.s_c, re, im);
-    r[2 * c] = re[0];
-    r[2 * c + 1] = im[0];
-  }
-  if (kind == KM) M::template normalize_obj<18>(r);
-  else M::template normalize_obj<6>(r);
-}
-
-// Accumulators of an object of w reals -> register values.
-template <class M>
-__device__ __forceinline__ void i_finish(typename M::R* d, const typename M::A* acc, int w) {
-  if constexpr (M::kScaled) {
-    if (w == 18) M::template finish_obj<18>(d, acc);
-    else if (w == 6) M::template finish_obj<6>(d, acc);
-    else M::template finish_obj<1>(d, acc);
   } else {
-    for (int r = 0; r < w; ++r) d[r] = M::finish(acc[r]);
+#pragma unroll
+    for (int c = 0; c < W / 2; ++c) {
+      typename M::R re[1], im[1];
+      Store<P_F64>::template load<M>(f.ptr, b + c * f.s_c, re, im);
+      r[2 * c] = re[0];
+      r[2 * c + 1] = im[0];
+    }
+  }
+  M::template normalize_obj<W>(r);
+}
+
+template <class M, int W>
+__device__ __forceinline__ void i_add(const IRegs<M>& R, const IIns& in, int sg) {
+  typename M::R x[W], y[W], d[W];
+  typename M::A acc[W];
+  R.template get<W>(in.a, x);
+  R.template get<W>(in.b, y);
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    M::template add<true, 1>(acc[r], x[r]);
+    if (sg > 0) M::template add<false, 1>(acc[r], y[r]);
+    else M::template add<false, -1>(acc[r], y[r]);
+  }
+  finish<M, W>(d, acc);
+  R.template put<W>(in.dst, d);
+}
+
+template <class M, int W>
+__device__ __forceinline__ void i_scale(const IRegs<M>& R, const IIns& in, const KParams& p) {
+  typename M::R x[W], d[W];
+  typename M::A acc[W];
+  R.template get<W>(in.a, x);
+  const typename M::R sc = M::scalar(p.sc[in.arg], p.sch[in.arg], p.scl[in.arg]);
+#pragma unroll
+  for (int r = 0; r < W; ++r) M::template fma<true, 1>(acc[r], sc, x[r]);
+  finish<M, W>(d, acc);
+  R.template put<W>(in.dst, d);
+}
+
+template <class M, int W>
+__device__ __forceinline__ void i_store(const FieldDesc& dst, int64_t s, int mu, const IRegs<M>& R,
+                                        int g) {
+  typename M::R z[W];
+  R.template get<W>(g, z);
+  const int64_t b = elem_base(dst, s, mu);
+  if constexpr (W == 1) {
+    StoreReal::template store_acc<M>(dst.ptr, b, M::to_acc(z[0]));
+  } else {
+#pragma unroll
+    for (int c = 0; c < W / 2; ++c) {
+      typename M::A re[1] = {M::to_acc(z[2 * c])}, im[1] = {M::to_acc(z[2 * c + 1])};
+      Store<P_F64>::template store_acc<M>(dst.ptr, b + c * dst.s_c, re, im);
+    }
   }
 }
 
 template <class M>
-__global__ void __launch_bounds__(256) k_interp(const __grid_constant__ KParams p,
+__global__ void __launch_bounds__(128) k_interp(const __grid_constant__ KParams p,
                                                 const __grid_constant__ IProg prog) {
-  using R = typename M::R;
-  using A = typename M::A;
+  using Rv = typename M::R;
+  using Av = typename M::A;
+  extern __shared__ __align__(16) unsigned char i_smem[];
+  const IRegs<M> R{reinterpret_cast<Rv*>(i_smem), (int)blockDim.x, (int)threadIdx.x};
   const int mu = blockIdx.y;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  R reg[kIRegs][18];
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.nvec; s += stride) {
     for (int pc = 0; pc < prog.n; ++pc) {
       const IIns in = prog.ins[pc];
-      R* d = reg[in.dst];
-      const R* x = reg[in.a];
-      const R* y = reg[in.b];
-      A acc[18];
       switch (in.op) {
-        case I_LOAD: i_load<M>(p.leaf[in.arg], in.b, s, mu, d); continue;
-        case I_MMUL: mm_acc<M, true, 1, false, false>(acc, x, y); break;
-        case I_MVMUL: mv_acc<M, true, 1, false>(acc, x, y); break;
-        case I_RMUL: M::template fma<true, 1>(acc[0], x[0], y[0]); break;
+        case I_LOAD: {
+          Rv v[18];
+          if (in.w == 18) {
+            i_load<M, 18>(p.leaf[in.arg], s, mu, v);
+            R.template put<18>(in.dst, v);
+          } else if (in.w == 6) {
+            i_load<M, 6>(p.leaf[in.arg], s, mu, v);
+            R.template put<6>(in.dst, v);
+          } else {
+            i_load<M, 1>(p.leaf[in.arg], s, mu, v);
+            R.template put<1>(in.dst, v);
+          }
+          break;
+        }
+        case I_MMUL: {
+          Rv x[18], y[18], d[18];
+          Av acc[18];
+          R.template get<18>(in.a, x);
+          R.template get<18>(in.b, y);
+          mm_acc<M, true, 1, false, false>(acc, x, y);
+          finish<M, 18>(d, acc);
+          R.template put<18>(in.dst, d);
+          break;
+        }
+        case I_MVMUL: {
+          Rv x[18], y[6], d[6];
+          Av acc[6];
+          R.template get<18>(in.a, x);
+          R.template get<6>(in.b, y);
+          mv_acc<M, true, 1, false>(acc, x, y);
+          finish<M, 6>(d, acc);
+          R.template put<6>(in.dst, d);
+          break;
+        }
+        case I_RMUL: {
+          Rv x[1], y[1], d[1];
+          Av acc[1];
+          R.template get<1>(in.a, x);
+          R.template get<1>(in.b, y);
+          M::template fma<true, 1>(acc[0], x[0], y[0]);
+          finish<M, 1>(d, acc);
+          R.template put<1>(in.dst, d);
+          break;
+        }
         case I_ADD:
-          for (int r = 0; r < in.w; ++r) {
-            M::template add<true, 1>(acc[r], x[r]);
-            M::template add<false, 1>(acc[r], y[r]);
-          }
+        case I_SUB: {
+          const int sg = in.op == I_ADD ? 1 : -1;
+          if (in.w == 18) i_add<M, 18>(R, in, sg);
+          else if (in.w == 6) i_add<M, 6>(R, in, sg);
+          else i_add<M, 1>(R, in, sg);
           break;
-        case I_SUB:
-          for (int r = 0; r < in.w; ++r) {
-            M::template add<true, 1>(acc[r], x[r]);
-            M::template add<false, -1>(acc[r], y[r]);
-          }
-          break;
+        }
         case I_SCALE: {
-          const R sc = M::scalar(p.sc[in.arg], p.sch[in.arg], p.scl[in.arg]);
-          for (int r = 0; r < in.w; ++r) M::template fma<true, 1>(acc[r], sc, x[r]);
+          if (in.w == 18) i_scale<M, 18>(R, in, p);
+          else if (in.w == 6) i_scale<M, 6>(R, in, p);
+          else i_scale<M, 1>(R, in, p);
           break;
         }
         default: {  // I_ADJ
-          R t[18];
+          Rv x[18], t[18];
+          R.template get<18>(in.a, x);
           adjoint<M>(t, x);
-          for (int r = 0; r < 18; ++r) d[r] = t[r];
-          continue;
+          R.template put<18>(in.dst, t);
+          break;
         }
       }
-      i_finish<M>(d, acc, in.w);
     }
-    const R* z = reg[prog.root];
-    const int64_t b = elem_base(p.dst, s, mu);
-    if (prog.root_kind == KR) {
-      StoreReal::template store_acc<M>(p.dst.ptr, b, M::to_acc(z[0]));
-    } else {
-      const int nc = prog.root_kind == KM ? 9 : 3;
-      for (int c = 0; c < nc; ++c) {
-        A re[1] = {M::to_acc(z[2 * c])}, im[1] = {M::to_acc(z[2 * c + 1])};
-        Store<P_F64>::template store_acc<M>(p.dst.ptr, b + c * p.dst.s_c, re, im);
-      }
-    }
+    if (prog.root_kind == KR) i_store<M, 1>(p.dst, s, mu, R, prog.root);
+    else if (prog.root_kind == KV) i_store<M, 6>(p.dst, s, mu, R, prog.root);
+    else i_store<M, 18>(p.dst, s, mu, R, prog.root);
   }
 }
 
@@ -131,6 +213,7 @@ struct Builder {
   IProg prog;
   bool busy[kIRegs] = {};
   int leaf_reg[kMaxLeaves];
+  int uses_left[kMaxLeaves] = {};  // leaf nodes of each slot not generated yet
   const Canon* c;
   int nscal = 0;
   int err = 0;
@@ -139,14 +222,16 @@ struct Builder {
     for (int r = 0; r < kIRegs; ++r)
       if (!busy[r]) {
         busy[r] = true;
+        if (r + 1 > prog.nregs) prog.nregs = r + 1;
         return r;
       }
     err = 1;
     return 0;
   }
+  // free register r unless it holds a leaf that is still to be used
   void release(int r) {
     for (int l = 0; l < kMaxLeaves; ++l)
-      if (leaf_reg[l] == r) return;  // leaf registers stay live
+      if (leaf_reg[l] == r && uses_left[l] > 0) return;
     busy[r] = false;
   }
   void emit(IIns in) {
@@ -164,11 +249,30 @@ struct Builder {
     return 0;
   }
 
+  void count_uses(const su3s_expr* e) {
+    if (e->op == 0) {
+      ++uses_left[slot_of(e->f)];
+      return;
+    }
+    if (e->a) count_uses(e->a);
+    if (e->b) count_uses(e->b);
+  }
+
   // returns the register holding the node's value
   int gen(const su3s_expr* e) {
     if (err) return 0;
     switch (e->op) {
-      case 0: return leaf_reg[slot_of(e->f)];
+      case 0: {  // a leaf: loaded at its first use
+        const int l = slot_of(e->f);
+        if (leaf_reg[l] < 0) {
+          const int r = alloc();
+          leaf_reg[l] = r;
+          const int kind = e->f->kind;
+          emit(IIns{I_LOAD, (int8_t)r, 0, (int8_t)kind, width(kind), (int8_t)l, {0, 0}});
+        }
+        --uses_left[l];
+        return leaf_reg[l];
+      }
       case 4: {
         int k = nscal++;  // factors numbered in the canonical (pre-order) order
         int a = gen(e->a);
@@ -199,6 +303,28 @@ struct Builder {
     }
   }
 };
+
+template <class M>
+cudaError_t launch_interp(const KParams& p, const IProg& prog, cudaStream_t st) {
+  // shared memory: nregs registers of 18 reals per thread; 128 threads per
+  // block while that fits in 200 KB, fewer for long programs
+  const size_t per_thread = (size_t)prog.nregs * 18 * sizeof(typename M::R);
+  int threads = 128;
+  while (threads > 32 && per_thread * threads > (200u << 10)) threads /= 2;
+  const size_t smem = per_thread * threads;
+  const void* k = (const void*)&k_interp<M>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 1;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)per_sm * sm_count();               // one wave, grid-stride
+  const int64_t need = (p.nvec + threads - 1) / threads;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  k_interp<M><<<dim3((unsigned)blocks, (unsigned)p.nmu), threads, smem, st>>>(p, prog);
+  return cudaGetLastError();
+}
 }  // namespace
 
 int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, cudaStream_t st) {
@@ -206,12 +332,7 @@ int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, 
   memset(&bld.prog, 0, sizeof bld.prog);
   bld.c = &c;
   for (int l = 0; l < kMaxLeaves; ++l) bld.leaf_reg[l] = -1;
-  for (size_t i = 0; i < c.leaves.size(); ++i) {
-    int r = bld.alloc();
-    bld.leaf_reg[i] = r;
-    int kind = c.leaves[i]->kind;
-    bld.emit(IIns{I_LOAD, (int8_t)r, 0, (int8_t)kind, Builder::width(kind), (int8_t)i, {0, 0}});
-  }
+  bld.count_uses(e);
   int root = bld.gen(e);
   if (bld.err)
     return fail(SU3S_EUNSUPPORTED, "expression too large for the interpreter (%d registers, %d steps)",
@@ -220,15 +341,9 @@ int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, 
   bld.prog.root_kind = c.kind;
   KParams p;
   build_params(c, dest, 1, &p);
-  const void* kern = math == MATH_F64  ? (const void*)&k_interp<MathF64>
-                     : math == MATH_FX ? (const void*)&k_interp<MathFX>
-                                       : (const void*)&k_interp<MathDF>;
-  dim3 grid, block;
-  launch_geometry(kern, p.nvec, p.nmu, &grid, &block);
-  if (math == MATH_F64) k_interp<MathF64><<<grid, block, 0, st>>>(p, bld.prog);
-  else if (math == MATH_FX) k_interp<MathFX><<<grid, block, 0, st>>>(p, bld.prog);
-  else k_interp<MathDF><<<grid, block, 0, st>>>(p, bld.prog);
-  cudaError_t ce = cudaGetLastError();
+  cudaError_t ce = math == MATH_F64  ? launch_interp<MathF64>(p, bld.prog, st)
+                   : math == MATH_FX ? launch_interp<MathFX>(p, bld.prog, st)
+                                     : launch_interp<MathDF>(p, bld.prog, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "interpreter kernel launch");
   return SU3S_OK;
 }
