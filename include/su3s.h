@@ -205,7 +205,9 @@ int su3s_field_download_stored(const su3s_field* f, void* host_stored, size_t nb
 
 /* Nodes are immutable and reference-counted: a node holds references to its
  * children, so the caller may free children after building a parent.  The
- * caller frees every handle it receives with su3s_expr_free.  Type rules:
+ * caller frees every handle it receives with su3s_expr_free.  A leaf refers to
+ * its field handle without owning it: the field handle (and its memory) must
+ * outlive every expression and batch that uses it.  Type rules:
  * matrix*matrix -> matrix, matrix*vector -> vector, real*real -> real;
  * add/sub need equal kinds; adj only on matrices; scale keeps the kind.
  * ETYPE on a violation, EINVAL on null arguments.  Trees are evaluated as
