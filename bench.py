@@ -67,14 +67,14 @@ MATH_ERR = {"fx": "7.8e-16 - 1.6e-15", "df32": "3.6e-14 - 5.7e-14", "f64": "3.3e
 # counters these are, bytes, algorithmic bytes of that launch).  A row missing
 # here reports traffic null.
 TRAFFIC_32 = {
-    "A2 z=a*b": ("k_eval_tma<MM,MathDF,0>", 411.3 * 1e6, 452984832),
-    "A4 z_mu=a_mu*b_mu": ("k_eval_tma<MM,MathDF,0>", 1775.9 * 1e6, 1811939328),
-    "A5 z=a*b+c*d": ("k_eval_tma<E1,MathDF,0>", 731.5 * 1e6, 754974720),
-    "A5 z=a*b*c+0.5*d": ("k_eval_tma<E2,MathDF,0>", 730.6 * 1e6, 754974720),
-    "A5 z=adj(a)*b-b*adj(a)": ("k_eval_tma<E3,MathDF,0>", 411.6 * 1e6, 452984832),
-    "A8 batch 64 lattices z=a*b+c*d": ("k_batch_tma<MathDF,E1>", 4606.2 * 1e6, 4622376960),
-    "A9 adjoint of z=a*b": ("k_adjoint_tma<MM,MathDF>", 706.0 * 1e6, 754974720),
-    "A9 adjoint of z=a*b+c*d": ("k_adjoint_tma<E1,MathDF>", 1304.2 * 1e6, 1358954496),
+    "A2 z=a*b": ("k_eval_tma<MM,MathDF,0>", 415.9 * 1e6, 452984832),
+    "A4 z_mu=a_mu*b_mu": ("k_eval_tma<MM,MathDF,0>", 1776.5 * 1e6, 1811939328),
+    "A5 z=a*b+c*d": ("k_eval_tma<E1,MathDF,0>", 731.7 * 1e6, 754974720),
+    "A5 z=a*b*c+0.5*d": ("k_eval_tma<E2,MathDF,0>", 731.2 * 1e6, 754974720),
+    "A5 z=adj(a)*b-b*adj(a)": ("k_eval_tma<E3,MathDF,0>", 415.1 * 1e6, 452984832),
+    "A8 batch 64 lattices z=a*b+c*d": ("k_batch_tma<MathDF,E1>", 4605.5 * 1e6, 4622376960),
+    "A9 adjoint of z=a*b": ("k_adjoint_tma<MM,MathDF>", 704.5 * 1e6, 754974720),
+    "A9 adjoint of z=a*b+c*d": ("k_adjoint_tma<E1,MathDFScalar>", 1304.6 * 1e6, 1358954496),
 }
 
 

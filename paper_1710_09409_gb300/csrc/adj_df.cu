@@ -4,19 +4,21 @@
 
 namespace su3s {
 
-template <class M>
+// M: arithmetic of the single products; MS: the same arithmetic for trees of
+// several products, whose reverse mode holds more operands at once
+template <class M, class MS>
 static void adj_set(int m) {
   using namespace cat;
   reg_adjoint<MM, M>(m);
   reg_adjoint<AdjMM, M>(m);
   reg_adjoint<MAdjM, M>(m);
   reg_adjoint<MV, M>(m);
-  reg_adjoint<E1, M>(m);
-  reg_adjoint<E1Sub, M>(m);
-  reg_adjoint<E1Lin, M>(m);
-  reg_adjoint<E2, M>(m);
-  reg_adjoint<MMM, M>(m);
-  reg_adjoint<E3, M>(m);
+  reg_adjoint<E1, MS>(m);
+  reg_adjoint<E1Sub, MS>(m);
+  reg_adjoint<E1Lin, MS>(m);
+  reg_adjoint<E2, MS>(m);
+  reg_adjoint<MMM, MS>(m);
+  reg_adjoint<E3, MS>(m);
   reg_adjoint<AddM, M>(m);
   reg_adjoint<ScaleM, M>(m);
   reg_adjoint<AdjM, M>(m);
@@ -25,6 +27,6 @@ static void adj_set(int m) {
   reg_adjoint<L2R, M>(m);
 }
 
-void register_adj_df() { adj_set<MathDF>(MATH_DF); }
+void register_adj_df() { adj_set<MathDF, MathDFScalar>(MATH_DF); }
 
 }  // namespace su3s

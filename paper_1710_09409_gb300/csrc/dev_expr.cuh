@@ -197,12 +197,63 @@ struct Ctx {
 };
 
 // ----------------------------------------------------------- primitives
+// Packed form of a 3x3 complex product for the pair arithmetic: output (i,k)
+// keeps (re, im) in the two lanes of one DAcc2.  Per inner index j, the terms
+//   re += SG xr yr,             im += SG sy xr ym        (A: y = (yr, ym))
+//   re += -SG sx sy xm ym,      im += SG sx xm yr        (B: y = (ym, yr))
+// enter in the scalar order (A then B, j = 0, 1, 2), so each lane repeats
+// MathDF's operations.  The signs ride on the x pairs, built once per element
+// of x for the three outputs of its row; the A pairs of y are the loaded
+// values themselves and only the swapped B pairs are extra registers.
+template <bool FIRST, int SG, bool AX, bool AY>
+__device__ __forceinline__ void mm_pairs(DAcc2* P, const df* x, const df* y) {
+  constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
+  constexpr int ar = SG, ai = SG * sy, br = -SG * sx * sy, bi = SG * sx;
+  df2 ya[9], yb[9];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int yi = AY ? (3 * k + j) : (3 * j + k);
+      const df yr = y[2 * yi], ym = y[2 * yi + 1];
+      ya[3 * j + k] = df2{make_float2(yr.h, ym.h), make_float2(yr.l, ym.l)};
+      yb[3 * j + k] = df2{make_float2(ym.h, yr.h), make_float2(ym.l, yr.l)};
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int xi = AX ? (3 * j + i) : (3 * i + j);
+      const df xr = x[2 * xi], xm = x[2 * xi + 1];
+      const df2 xa{make_float2(ar > 0 ? xr.h : -xr.h, ai > 0 ? xr.h : -xr.h),
+                   make_float2(ar > 0 ? xr.l : -xr.l, ai > 0 ? xr.l : -xr.l)};
+      const df2 xb{make_float2(br > 0 ? xm.h : -xm.h, bi > 0 ? xm.h : -xm.h),
+                   make_float2(br > 0 ? xm.l : -xm.l, bi > 0 ? xm.l : -xm.l)};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        DAcc2& a = P[3 * i + k];
+        if (FIRST && j == 0) df2_first(a, xa, ya[3 * j + k]);
+        else df2_fma(a, xa, ya[3 * j + k]);
+        df2_fma(a, xb, yb[3 * j + k]);
+      }
+    }
+}
+
 // z (+)= SG * op(x) * op(y), 3x3 complex; op = adjoint when AX / AY.
 template <class M, bool FIRST, int SG, bool AX, bool AY>
 __device__ __forceinline__ void mm_acc(typename M::A* z, const typename M::R* x,
                                        const typename M::R* y) {
   constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
-  if constexpr (M::kScaled) {
+  if constexpr (M::kPaired) {
+    DAcc2 P[9];
+    if constexpr (!FIRST) {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) P[e] = dacc2_get(z[2 * e], z[2 * e + 1]);
+    }
+    mm_pairs<FIRST, SG, AX, AY>(P, x, y);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) dacc2_put(z[2 * e], z[2 * e + 1], P[e]);
+  } else if constexpr (M::kScaled) {
     // integer multiply-adds have a long latency: advance the 18 independent
     // accumulators together, one inner index j at a time
 #pragma unroll
@@ -303,6 +354,17 @@ template <class M, int SG, bool AX, bool AY>
 __device__ __forceinline__ void mm_combine(typename M::A* z, const typename M::R* x,
                                            const typename M::R* y) {
   constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
+  if constexpr (M::kPaired) {
+    DAcc2 P[9];
+    mm_pairs<true, 1, AX, AY>(P, x, y);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      DAcc2 a = dacc2_get(z[2 * e], z[2 * e + 1]);
+      df2_combine<SG>(a, P[e]);
+      dacc2_put(z[2 * e], z[2 * e + 1], a);
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll

@@ -25,6 +25,10 @@
 //                scaled to units of the last place gives the low 29 bits.
 //            Error per output ~2^-46 * sum_t |x_t y_t| + 2^-52 |z|.  Needs all
 //            magnitudes below 2^126; magnitudes below 2^-126 may be flushed.
+//            3x3 complex products run the real and imaginary accumulations of
+//            an output in the two lanes of packed FP32 instructions (same
+//            operations per lane, fewer issued instructions); MathDFScalar is
+//            the scalar-issue form for kernels short of registers.
 //   MathFX   FP64-accurate arithmetic on the integer multiply-add units
 //            (shared-exponent fixed point):
 //              * the reals of one site object (a matrix, a vector, a real)
@@ -100,6 +104,7 @@ struct MathF64 {
   using R = double;   // one real component
   using A = double;   // accumulator
   static constexpr bool kScaled = false;  // every term shares one scale
+  static constexpr bool kPaired = false;  // no packed (re, im) products
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return __hiloint2double((int)hi, (int)lo);
   }
@@ -139,6 +144,7 @@ struct MathDF {
   using R = df;
   using A = DAcc;
   static constexpr bool kScaled = false;
+  static constexpr bool kPaired = true;   // complex products in packed (re, im) lanes
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return df_split_bits(lo, hi);
   }
@@ -215,6 +221,114 @@ struct MathDF {
   }
 };
 
+// The same arithmetic issued as scalar instructions only, for kernels whose
+// register budget has no room for the packed operand pairs (the reverse mode
+// of multi-product trees, the hopping term on matrices, the interpreter):
+// there the extra registers of the pairs cost more than the packed
+// instructions save.  Results are identical to MathDF's.
+struct MathDFScalar : MathDF {
+  static constexpr bool kPaired = false;
+};
+
+// --------------------------------------------- MathDF, packed (re, im) lanes
+// The real and imaginary parts of one complex output advance together in the
+// two lanes of the packed FP32 instructions of sm_100 and later (two FP32
+// operations per issued instruction).  Each lane performs exactly the
+// operations of MathDF::fma / MathDF::combine in the same order, so the packed
+// path gives the same values as the scalar one.  Adds, subtracts and FMAs are
+// packed (PTX with an explicit round-to-nearest-even modifier); the leading
+// products stay two scalar multiplies.  With CUDA 13.0 on sm_103a a packed
+// multiply whose result feeds a packed add lost TwoSum's exact error term (the
+// 3x3 product came out with FP32 accuracy, ~1e-8), while scalar multiplies
+// with packed adds, or packed multiplies with scalar adds, gave the scalar
+// arithmetic's values; the scalar multiplies cost one instruction more per
+// term.  -bp is formed as S - s, the exact negation of s - S under
+// round-to-nearest-even.
+struct DAcc2 {
+  float2 S, lo;  // .x = real part's accumulator, .y = imaginary part's
+};
+struct df2 {
+  float2 h, l;   // lane-wise leading and trailing parts
+};
+
+// lane-wise product as two scalar multiplies (see above)
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// a * b + c, one rounding per lane
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+__device__ __forceinline__ DAcc2 dacc2_get(const DAcc& re, const DAcc& im) {
+  return DAcc2{make_float2(re.S, im.S), make_float2(re.lo, im.lo)};
+}
+__device__ __forceinline__ void dacc2_put(DAcc& re, DAcc& im, const DAcc2& a) {
+  re.S = a.S.x;
+  im.S = a.S.y;
+  re.lo = a.lo.x;
+  im.lo = a.lo.y;
+}
+
+// a = x * y lane-wise (MathDF::fma with FIRST)
+__device__ __forceinline__ void df2_first(DAcc2& a, const df2& x, const df2& y) {
+  const float2 p = f2_mul(x.h, y.h);
+  const float2 np = f2_mul(p, make_float2(-1.0f, -1.0f));  // -p, exact
+  float2 q = f2_fma(x.h, y.h, np);            // exact error of the leading product
+  q = f2_fma(x.h, y.l, q);
+  q = f2_fma(x.l, y.h, q);
+  a.S = p;
+  a.lo = q;
+}
+
+// a += x * y lane-wise (MathDF::fma without FIRST)
+__device__ __forceinline__ void df2_fma(DAcc2& a, const df2& x, const df2& y) {
+  const float2 p = f2_mul(x.h, y.h);
+  const float2 s = f2_add(a.S, p);            // TwoSum(S, xh*yh)
+  const float2 nbp = f2_sub(a.S, s);          // -bp
+  const float2 ap = f2_add(s, nbp);           // s - bp
+  const float2 db = f2_fma(x.h, y.h, nbp);    // exact product minus bp, one rounding
+  const float2 da = f2_sub(a.S, ap);
+  float2 t = f2_add(da, db);
+  t = f2_fma(x.l, y.h, t);
+  t = f2_fma(x.h, y.l, t);
+  a.S = s;
+  a.lo = f2_add(a.lo, t);
+}
+
+// a += SG * b lane-wise (MathDF::combine)
+template <int SG>
+__device__ __forceinline__ void df2_combine(DAcc2& a, const DAcc2& b) {
+  const float2 s = SG > 0 ? f2_add(a.S, b.S) : f2_sub(a.S, b.S);
+  const float2 nbp = f2_sub(a.S, s);          // -bp
+  const float2 ap = f2_add(s, nbp);           // s - bp
+  const float2 db = SG > 0 ? f2_add(b.S, nbp) : f2_sub(nbp, b.S);  // sg*bS - bp
+  const float2 da = f2_sub(a.S, ap);
+  float2 t = f2_add(da, db);
+  t = SG > 0 ? f2_add(t, b.lo) : f2_sub(t, b.lo);
+  a.S = s;
+  a.lo = f2_add(a.lo, t);
+}
+
 // -------------------------------------------------------------- MathFX
 // One real of an object: value (h * 2^25 + l * 2^-6) * 2^(e - 1075), with
 // |h| <= 2^28, |l| < 2^31 and l a multiple of 64 (the low 25 bits of m,
@@ -252,6 +366,7 @@ struct MathFX {
   using R = fxr;
   using A = FAcc;
   static constexpr bool kScaled = true;  // terms of different objects differ in scale
+  static constexpr bool kPaired = false;
 
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return fxr{(int)hi, (int)lo, 0};
@@ -391,6 +506,7 @@ struct MathF32 {
   using R = float;
   using A = float;
   static constexpr bool kScaled = false;
+  static constexpr bool kPaired = false;
   __device__ static __forceinline__ R finish(const A& a) { return a; }
   __device__ static __forceinline__ A to_acc(const R& x) { return x; }
   __device__ static __forceinline__ A zero() { return 0.0f; }

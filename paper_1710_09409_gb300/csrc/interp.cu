@@ -343,7 +343,7 @@ int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, 
   build_params(c, dest, 1, &p);
   cudaError_t ce = math == MATH_F64  ? launch_interp<MathF64>(p, bld.prog, st)
                    : math == MATH_FX ? launch_interp<MathFX>(p, bld.prog, st)
-                                     : launch_interp<MathDF>(p, bld.prog, st);
+                                     : launch_interp<MathDFScalar>(p, bld.prog, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "interpreter kernel launch");
   return SU3S_OK;
 }

@@ -288,7 +288,7 @@ SU3S_EXPORT int su3s_hop(su3s_field* dest, const su3s_field* U, const su3s_field
   const bool mat = v->kind == SU3S_MATRIX;
   if (m == MATH_F64) ce = mat ? launch_hop<MathF64, KM>(dest, U, v, st) : launch_hop<MathF64, KV>(dest, U, v, st);
   else if (m == MATH_FX) ce = mat ? launch_hop<MathFX, KM>(dest, U, v, st) : launch_hop<MathFX, KV>(dest, U, v, st);
-  else ce = mat ? launch_hop<MathDF, KM>(dest, U, v, st) : launch_hop<MathDF, KV>(dest, U, v, st);
+  else ce = mat ? launch_hop<MathDFScalar, KM>(dest, U, v, st) : launch_hop<MathDF, KV>(dest, U, v, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "hopping-term kernel launch");
   return SU3S_OK;
 }
