@@ -305,11 +305,52 @@ __device__ __forceinline__ void mm_acc(typename M::A* z, const typename M::R* x,
   }
 }
 
+// Packed form of op(x) * v for the pair arithmetic, as mm_pairs: output i
+// keeps (re, im) in one DAcc2; per j the terms xr (vr, vm) and xm (vm, vr)
+// enter in the scalar order with the signs on the x pairs.
+template <bool FIRST, int SG, bool AX>
+__device__ __forceinline__ void mv_pairs(DAcc2* P, const df* x, const df* v) {
+  constexpr int sx = AX ? -1 : 1;
+  constexpr int br = -SG * sx, bi = SG * sx;
+  df2 va[3], vb[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const df vr = v[2 * j], vm = v[2 * j + 1];
+    va[j] = df2{make_float2(vr.h, vm.h), make_float2(vr.l, vm.l)};
+    vb[j] = df2{make_float2(vm.h, vr.h), make_float2(vm.l, vr.l)};
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int xi = AX ? (3 * j + i) : (3 * i + j);
+      const df xr = x[2 * xi], xm = x[2 * xi + 1];
+      const df2 xa{make_float2(SG > 0 ? xr.h : -xr.h, SG > 0 ? xr.h : -xr.h),
+                   make_float2(SG > 0 ? xr.l : -xr.l, SG > 0 ? xr.l : -xr.l)};
+      const df2 xb{make_float2(br > 0 ? xm.h : -xm.h, bi > 0 ? xm.h : -xm.h),
+                   make_float2(br > 0 ? xm.l : -xm.l, bi > 0 ? xm.l : -xm.l)};
+      if (FIRST && j == 0) df2_first(P[i], xa, va[j]);
+      else df2_fma(P[i], xa, va[j]);
+      df2_fma(P[i], xb, vb[j]);
+    }
+}
+
 // z (+)= SG * op(x) * v, x 3x3, v 3-vector.
 template <class M, bool FIRST, int SG, bool AX>
 __device__ __forceinline__ void mv_acc(typename M::A* z, const typename M::R* x,
                                        const typename M::R* v) {
   constexpr int sx = AX ? -1 : 1;
+  if constexpr (M::kPaired) {
+    DAcc2 P[3];
+    if constexpr (!FIRST) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) P[i] = dacc2_get(z[2 * i], z[2 * i + 1]);
+    }
+    mv_pairs<FIRST, SG, AX>(P, x, v);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dacc2_put(z[2 * i], z[2 * i + 1], P[i]);
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     typename M::A& re = z[2 * i];
@@ -393,6 +434,17 @@ template <class M, int SG, bool AX>
 __device__ __forceinline__ void mv_combine(typename M::A* z, const typename M::R* x,
                                            const typename M::R* v) {
   constexpr int sx = AX ? -1 : 1;
+  if constexpr (M::kPaired) {
+    DAcc2 P[3];
+    mv_pairs<true, 1, AX>(P, x, v);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      DAcc2 a = dacc2_get(z[2 * i], z[2 * i + 1]);
+      df2_combine<SG>(a, P[i]);
+      dacc2_put(z[2 * i], z[2 * i + 1], a);
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     typename M::A re, im;
