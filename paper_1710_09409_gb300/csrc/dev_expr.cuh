@@ -349,24 +349,24 @@ __device__ __forceinline__ void mv_acc(typename M::A* z, const typename M::R* x,
     mv_pairs<FIRST, SG, AX>(P, x, v);
 #pragma unroll
     for (int i = 0; i < 3; ++i) dacc2_put(z[2 * i], z[2 * i + 1], P[i]);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    typename M::A& re = z[2 * i];
-    typename M::A& im = z[2 * i + 1];
+    for (int i = 0; i < 3; ++i) {
+      typename M::A& re = z[2 * i];
+      typename M::A& im = z[2 * i + 1];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int xi = AX ? (3 * j + i) : (3 * i + j);
-      if (FIRST && j == 0) {
-        M::template fma<true, SG>(re, x[2 * xi], v[2 * j]);
-        M::template fma<true, SG>(im, x[2 * xi], v[2 * j + 1]);
-      } else {
-        M::template fma<false, SG>(re, x[2 * xi], v[2 * j]);
-        M::template fma<false, SG>(im, x[2 * xi], v[2 * j + 1]);
+      for (int j = 0; j < 3; ++j) {
+        const int xi = AX ? (3 * j + i) : (3 * i + j);
+        if (FIRST && j == 0) {
+          M::template fma<true, SG>(re, x[2 * xi], v[2 * j]);
+          M::template fma<true, SG>(im, x[2 * xi], v[2 * j + 1]);
+        } else {
+          M::template fma<false, SG>(re, x[2 * xi], v[2 * j]);
+          M::template fma<false, SG>(im, x[2 * xi], v[2 * j + 1]);
+        }
+        M::template fma<false, -SG * sx>(re, x[2 * xi + 1], v[2 * j + 1]);
+        M::template fma<false, SG * sx>(im, x[2 * xi + 1], v[2 * j]);
       }
-      M::template fma<false, -SG * sx>(re, x[2 * xi + 1], v[2 * j + 1]);
-      M::template fma<false, SG * sx>(im, x[2 * xi + 1], v[2 * j]);
     }
   }
 }
@@ -404,30 +404,30 @@ __device__ __forceinline__ void mm_combine(typename M::A* z, const typename M::R
       df2_combine<SG>(a, P[e]);
       dacc2_put(z[2 * e], z[2 * e + 1], a);
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      typename M::A re, im;
+      for (int k = 0; k < 3; ++k) {
+        typename M::A re, im;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int xi = AX ? (3 * j + i) : (3 * i + j);
-        const int yi = AY ? (3 * k + j) : (3 * j + k);
-        if (j == 0) {
-          M::template fma<true, 1>(re, x[2 * xi], y[2 * yi]);
-          M::template fma<true, sy>(im, x[2 * xi], y[2 * yi + 1]);
-        } else {
-          M::template fma<false, 1>(re, x[2 * xi], y[2 * yi]);
-          M::template fma<false, sy>(im, x[2 * xi], y[2 * yi + 1]);
+        for (int j = 0; j < 3; ++j) {
+          const int xi = AX ? (3 * j + i) : (3 * i + j);
+          const int yi = AY ? (3 * k + j) : (3 * j + k);
+          if (j == 0) {
+            M::template fma<true, 1>(re, x[2 * xi], y[2 * yi]);
+            M::template fma<true, sy>(im, x[2 * xi], y[2 * yi + 1]);
+          } else {
+            M::template fma<false, 1>(re, x[2 * xi], y[2 * yi]);
+            M::template fma<false, sy>(im, x[2 * xi], y[2 * yi + 1]);
+          }
+          M::template fma<false, -sx * sy>(re, x[2 * xi + 1], y[2 * yi + 1]);
+          M::template fma<false, sx>(im, x[2 * xi + 1], y[2 * yi]);
         }
-        M::template fma<false, -sx * sy>(re, x[2 * xi + 1], y[2 * yi + 1]);
-        M::template fma<false, sx>(im, x[2 * xi + 1], y[2 * yi]);
+        M::template combine<SG>(z[2 * (3 * i + k)], re);
+        M::template combine<SG>(z[2 * (3 * i + k) + 1], im);
       }
-      M::template combine<SG>(z[2 * (3 * i + k)], re);
-      M::template combine<SG>(z[2 * (3 * i + k) + 1], im);
-    }
+  }
 }
 
 template <class M, int SG, bool AX>
@@ -443,26 +443,26 @@ __device__ __forceinline__ void mv_combine(typename M::A* z, const typename M::R
       df2_combine<SG>(a, P[i]);
       dacc2_put(z[2 * i], z[2 * i + 1], a);
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    typename M::A re, im;
+    for (int i = 0; i < 3; ++i) {
+      typename M::A re, im;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int xi = AX ? (3 * j + i) : (3 * i + j);
-      if (j == 0) {
-        M::template fma<true, 1>(re, x[2 * xi], v[2 * j]);
-        M::template fma<true, 1>(im, x[2 * xi], v[2 * j + 1]);
-      } else {
-        M::template fma<false, 1>(re, x[2 * xi], v[2 * j]);
-        M::template fma<false, 1>(im, x[2 * xi], v[2 * j + 1]);
+      for (int j = 0; j < 3; ++j) {
+        const int xi = AX ? (3 * j + i) : (3 * i + j);
+        if (j == 0) {
+          M::template fma<true, 1>(re, x[2 * xi], v[2 * j]);
+          M::template fma<true, 1>(im, x[2 * xi], v[2 * j + 1]);
+        } else {
+          M::template fma<false, 1>(re, x[2 * xi], v[2 * j]);
+          M::template fma<false, 1>(im, x[2 * xi], v[2 * j + 1]);
+        }
+        M::template fma<false, -sx>(re, x[2 * xi + 1], v[2 * j + 1]);
+        M::template fma<false, sx>(im, x[2 * xi + 1], v[2 * j]);
       }
-      M::template fma<false, -sx>(re, x[2 * xi + 1], v[2 * j + 1]);
-      M::template fma<false, sx>(im, x[2 * xi + 1], v[2 * j]);
+      M::template combine<SG>(z[2 * i], re);
+      M::template combine<SG>(z[2 * i + 1], im);
     }
-    M::template combine<SG>(z[2 * i], re);
-    M::template combine<SG>(z[2 * i + 1], im);
   }
 }
 
