@@ -756,7 +756,7 @@ def run_studies(su3s, synth, torch, stream, which):
         torch.cuda.empty_cache()
 
     if "stencil" in which:
-        # nearest-neighbour operations (Sec. 7): the hopping term and the Cshift;
+        # nearest-neighbour operations (Sec. 6, Summary and Outlook): the hopping term and the Cshift;
         # algorithmic bytes: every input object once, the output once
         for dims in ((32, 32, 32, 32), (48, 48, 48, 48)):
             v = synth.volume(dims)

@@ -166,9 +166,14 @@ int su3s_field_download(const su3s_field* f, double* host_canonical, size_t n_do
  *     8^4 Lorentz field); larger fields return ESHAPE with a message pointing
  *     to su3s_field_download.
  *   - The staging array is held by every GPU on which the library is used
- *     until the process exits.  Its device address is looked up on the first
- *     call made on each device (with that device current); make that first
- *     call before any stream capture.
+ *     until the process exits.  It is placed in device memory when the
+ *     library's module that holds it is loaded on a device, which
+ *     su3s_field_wrap does for the current device (field creation is allowed
+ *     to allocate), so the download finds its address ready.  Only a call on
+ *     a device where no field was ever wrapped loads the module itself; make
+ *     such a call before any stream capture and before the device's memory is
+ *     exhausted.  A device reset while the library is loaded is not
+ *     supported (the cached address would go stale).
  *   - Every call shares the array and it keeps the last call's contents; calls
  *     whose work overlaps on the GPU (other streams, other threads) race on it.
  *     Calls ordered on one stream do not.
@@ -429,10 +434,11 @@ int su3s_field_redot(const su3s_field* x, const su3s_field* y, double* dev_out, 
 int su3s_reunitarize(su3s_field* dst, const su3s_field* src, void* stream);
 
 /* ------------------------------------------------------------------------
- * Nearest-neighbour operations (arXiv:1710.09409 Sec. 7: the Dslash operator
- * and the Cshift operations outside the expression templates are the paper's
- * next step).  Sites are s = x + Lx (y + Ly (z + Lz t)); directions 0..3 are
- * x, y, z, t; every direction is periodic.
+ * Nearest-neighbour operations (arXiv:1710.09409 Sec. 6, Summary and
+ * Outlook: the Dslash operator and the Cshift operations outside the
+ * expression templates are the paper's next step).  Sites are
+ * s = x + Lx (y + Ly (z + Lz t)); directions 0..3 are x, y, z, t; every
+ * direction is periodic.
  * ---------------------------------------------------------------------- */
 
 /* dst(x) = src(x + shift * e_dim) at every site, link and component: a copy

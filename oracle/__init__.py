@@ -15,8 +15,8 @@ for the definitions):
   c12_expand      third row of an SU(3) matrix rebuilt from rows 0 and 1
   redot           sum_x Re tr(X^dagger Y)
   reunitarize     projection to SU(3): Gram-Schmidt over rows, det phase removed
-  cshift          Sec. 7 (Cshift): circular shift along one lattice direction
-  hop             Sec. 7 (Dslash): colour part of the nearest-neighbour
+  cshift          Sec. 6 (Cshift): circular shift along one lattice direction
+  hop             Sec. 6 (Dslash): colour part of the nearest-neighbour
                   hopping term, sum_mu U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu)
 
 Parity status: every function here is pinned by the CPU tests in
@@ -255,7 +255,7 @@ def _dims(dims):
 
 
 def cshift(x, dims, dim, shift):
-    """dst(s) = x(s + shift * e_dim), periodic (Sec. 7's Cshift).  x: canonical
+    """dst(s) = x(s + shift * e_dim), periodic (the Cshift of Sec. 6).  x: canonical
     field array whose first axis runs over sites (all links and components of
     a site follow)."""
     x = _c(x)
@@ -268,7 +268,7 @@ def cshift(x, dims, dim, shift):
 
 def hop(u, x, dims):
     """out(s) = sum_mu U_mu(s) x(s+mu) + U_mu(s-mu)^dagger x(s-mu): the colour part
-    of the Dslash hopping term (Sec. 7).  u: (V*4, 3, 3, 2) links; x: (V, 3, 3, 2)
+    of the Dslash hopping term (Sec. 6).  u: (V*4, 3, 3, 2) links; x: (V, 3, 3, 2)
     matrices or (V, 3, 2) vectors."""
     u, x = _c(u), _c(x)
     v = int(np.prod(dims))

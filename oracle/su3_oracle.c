@@ -36,9 +36,9 @@
  *   oracle_cshift  circular shift of a field along one lattice direction,
  *                  dst(x) = src(x + shift * e_dim) with periodic wrap (the
  *                  Cshift operation the paper names as the next step beside
- *                  its Dslash port, Sec. 7).
+ *                  its Dslash port, Sec. 6).
  *   oracle_hop     the colour part of the Wilson Dslash operator, the
- *                  nearest-neighbour hopping term of Sec. 7:
+ *                  nearest-neighbour hopping term of Sec. 6:
  *                  out(x) = sum_mu [ U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu) ],
  *                  v a colour vector or a colour matrix field, U the 4 links.
  *                  Site order: s = x + Lx*(y + Ly*(z + Lz*t)); directions

@@ -23,14 +23,21 @@ namespace su3s {
 // code here; su3s_device_error reads and clears it.
 __device__ int su3s_device_error_flag = 0;
 
+// Address of the error word on the current device: every device that loads
+// the library has its own copy, looked up once per device (with that device
+// current) and cached.  Null if the lookup fails.
 static int* device_error_ptr() {
-  static int* ptr = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static int* ptrs[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptrs[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, su3s_device_error_flag) == cudaSuccess) ptr = (int*)p;
-  });
-  return ptr;
+    if (cudaGetSymbolAddress(&p, su3s_device_error_flag) == cudaSuccess) ptrs[dev] = (int*)p;
+  }
+  return ptrs[dev];
 }
 
 // -1: choose per launch (TMA-staged where the layout allows), 0: plain loads, 1: TMA-staged
@@ -634,6 +641,11 @@ SU3S_EXPORT int su3s_field_wrap(const su3s_lattice* lat, int kind, int nmu, int 
   f->bytes = bytes;
   fill_desc(f);
   encode_tmap(f);
+  // Field creation may allocate: resolve here, on the current device, the
+  // static staging array of su3s_field_download_static (which loads the
+  // module holding it), so that the download itself never has to.  A failure
+  // is reported by that download, not here.
+  prepare_static_stage();
   *out = f;
   return ok();
 }

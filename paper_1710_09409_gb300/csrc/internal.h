@@ -109,6 +109,10 @@ cudaError_t launch_unpack(const su3s_field* f, double* canon, cudaStream_t st);
 cudaError_t launch_put_stored(const su3s_field* f, const void* src, cudaStream_t st);
 cudaError_t launch_get_stored(const su3s_field* f, void* dst, cudaStream_t st);
 
+// look up the static staging array of the no-allocation download on the
+// current device (noalloc.cu); returns a status, cached per device
+int prepare_static_stage();
+
 // stream-ordered scratch from the library's memory pool
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
 cudaError_t scratch_free(void* p, cudaStream_t st);

@@ -23,7 +23,11 @@ constexpr size_t kStaticStageDoubles = (size_t)2 << 20;
 static __device__ __align__(256) double g_static_stage[kStaticStageDoubles];
 
 // Device address of the staging array on the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached.  The first lookup on a
+// device loads this file's module there, which places the array in device
+// memory; su3s_field_wrap does it (field creation may allocate), so a
+// download of a wrapped field finds the address cached.  The cache is not
+// invalidated: a device reset while the library is loaded is not supported.
 static int static_stage_ptr(double** out) {
   constexpr int kMaxDevices = 64;
   static std::mutex mu;
@@ -41,6 +45,11 @@ static int static_stage_ptr(double** out) {
   }
   *out = ptrs[dev];
   return SU3S_OK;
+}
+
+int prepare_static_stage() {
+  double* p = nullptr;
+  return static_stage_ptr(&p);
 }
 
 }  // namespace su3s

@@ -1,7 +1,7 @@
 // Nearest-neighbour operations: the Cshift and the colour part of the Dslash
 // hopping term, which the paper names as the next step beyond its site-local
-// expression engine (Sec. 7: porting Grid's Dslash operator, whose Cshift
-// operations lie outside the expression templates).
+// expression engine (Sec. 6, Summary and Outlook: porting Grid's Dslash
+// operator, whose Cshift operations lie outside the expression templates).
 //
 //   su3s_cshift  dst(x) = src(x + shift e_dim), periodic in every direction:
 //                a gather of whole site objects in their storage format.

@@ -1,4 +1,4 @@
-"""GPU parity of the nearest-neighbour operations (Sec. 7: Cshift and the
+"""GPU parity of the nearest-neighbour operations (Sec. 6, Summary and Outlook: Cshift and the
 colour part of the Dslash hopping term) against the CPU oracle.
 
   * su3s_cshift is a copy of stored objects: its stored values are bit exact

@@ -401,7 +401,7 @@ def test_generator_gaussian_moments():
     assert s.min() > -1.0 and s.max() < 1.0 and abs(s.mean()) < 0.01
 
 
-# ------------------------------------------------ neighbours (Sec. 7)
+# ------------------------------------------------ neighbours (Sec. 6)
 STENCIL_DIMS = [(3, 2, 5, 4), (1, 3, 1, 2), (4, 4, 4, 4)]
 
 

@@ -75,3 +75,23 @@ def test_static_download_rejects_fields_beyond_the_limit(gpu_lib):
     rc = L.su3s_field_download_static(big._h, ctypes.c_void_p(out.ctypes.data), out.size, None)
     assert rc == 3
     assert b"static staging area" in L.su3s_last_error()
+
+
+def test_static_download_leaves_device_memory_untouched(gpu_lib):
+    # The property the entry point exists for: after a warm-up call (which
+    # loads the unpack kernel's code), further calls change neither the
+    # device's free memory nor torch's allocator.
+    su3s = gpu_lib
+    dims = (8, 8, 8, 8)
+    lat = su3s.Lattice(dims)
+    a = su3s.Field(lat, su3s.MATRIX, 4, su3s.F64)
+    a.upload(synth.su3(SEED, 2, synth.volume(dims) * 4))
+    first = _download_static(su3s, a)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(3):
+        assert np.array_equal(_download_static(su3s, a), first)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
