@@ -255,9 +255,9 @@ int su3s_eval(su3s_field* dest, const su3s_expr* e, void* stream);
  *                   FP32 values (integer bit operations, no FP64 instruction),
  *                   products and sums use error-free transformations in FP32,
  *                   and results are re-assembled into FP64 bit patterns.
- *                   Error per output <= ~2^-46 * sum_t |x_t y_t| (+ 2^-52 |z|);
- *                   needs every |input| and |intermediate| < 2^126, and values
- *                   below 2^-126 in magnitude may be flushed to zero.
+ *                   Error per output <= ~2^-46 * sum_t |x_t y_t| (+ 2^-52 |z|),
+ *                   plus an absolute error below 2^-126 times the other
+ *                   factors' magnitudes for inputs below 2^-126 (flushed).
  *   SU3S_MATH_FX    the reals of each site object (matrix, vector, real)
  *                   share the exponent of the object's largest element and
  *                   become 53-bit signed integers; products are exact 32-bit
@@ -270,6 +270,17 @@ int su3s_eval(su3s_field* dest, const su3s_expr* e, void* stream);
  *                   are flushed to zero; results must stay below 2^960 in
  *                   magnitude, and results below 2^-1022 are returned with an
  *                   absolute error below 2^-1022.
+ * Range guard of SU3S_MATH_DF32 and SU3S_MATH_FX (every kernel that evaluates
+ * in them, forward, reverse mode, batch, interpreter and neighbour terms):
+ * each site's FP64 inputs (leaves, dL/dZ and the real factors of the tree)
+ * are checked as they are read.  A site with an input that is NaN, +-Inf or
+ * at least 2^t(d) in magnitude, t(d) = floor((120 - 3 (d - 1)) / d) for a
+ * tree whose terms have at most d factors (d = 2: 2^58, d = 3: 2^38), is
+ * evaluated again in native FP64 (SU3S_MATH_F64) in the same kernel before
+ * anything of it is stored.  Such sites therefore get IEEE results (NaN and
+ * Inf propagate, large values do not overflow early); sites in range keep
+ * the arithmetic's own results.  Nothing is reported: no status, no error
+ * word.  The bound keeps every intermediate of a site in range below 2^127.
  * Ignored for reduced-precision storage.  EINVAL for another value. */
 int su3s_eval_math(su3s_field* dest, const su3s_expr* e, int math, void* stream);
 
@@ -393,7 +404,9 @@ int su3s_batch_destroy(su3s_batch* b);
  * the tree's value is the field `grad_out` (same shape as the tree's value;
  * gradient convention dL/dRe + i dL/dIm).  Writes dL/d(leaf) for the unique
  * leaves of `e` in order of first appearance into grad_leaves[k]
- * (overwritten, not accumulated; NULL entries are skipped).  nleaves must
+ * (overwritten, not accumulated; NULL entries are skipped; a gradient field
+ * that overlaps a leaf, grad_out or another gradient returns EINVAL, since
+ * leaves are read while gradients are written).  nleaves must
  * equal the number of unique leaves.  For z = a*b this is dA = G B^dagger,
  * dB = A^dagger G; sums, scalings and adjoints follow the chain rule.
  * One pass: every leaf and grad_out is read once, every gradient written

@@ -514,6 +514,11 @@ int build_params(const Canon& c, const su3s_field* dest, int vps, KParams* p) {
   for (size_t k = 0; k < c.scalars.size(); ++k) {
     p->sc[k] = c.scalars[k];
     split_scalar(c.scalars[k], &p->sch[k], &p->scl[k]);
+    // the real factors are inputs of every site: they open its range guard
+    uint64_t bits;
+    memcpy(&bits, &c.scalars[k], sizeof bits);
+    const uint32_t hi = (uint32_t)(bits >> 32) & 0x7FFFFFFFu;
+    if (hi > p->gscal) p->gscal = hi;
   }
   p->nvec = dest->Vpad / vps;
   p->nmu = dest->nmu;
@@ -1050,6 +1055,23 @@ static int prepare_adjoint(const su3s_expr* e, const su3s_field* gout, su3s_fiel
       if (gleaves[i]->kind != c.leaves[i]->kind)
         return fail(SU3S_ETYPE, "gradient %zu has the wrong kind", i);
     }
+  }
+  // Gradients are written while leaves and dL/dZ are still being read (and a
+  // site out of the FP64-accurate range reads them again): no overlap.
+  const auto overlap = [](const su3s_field* a, const su3s_field* b) {
+    const char* pa = (const char*)a->ptr;
+    const char* pb = (const char*)b->ptr;
+    return pa < pb + b->bytes && pb < pa + a->bytes;
+  };
+  for (size_t i = 0; gleaves && i < c.leaves.size(); ++i) {
+    if (!gleaves[i]) continue;
+    bool clash = overlap(gleaves[i], gout);
+    for (size_t j = 0; j < c.leaves.size(); ++j) {
+      clash = clash || overlap(gleaves[i], c.leaves[j]);
+      if (j != i && gleaves[j]) clash = clash || overlap(gleaves[i], gleaves[j]);
+    }
+    if (clash)
+      return fail(SU3S_EINVAL, "gradient %zu overlaps a leaf, dL/dZ or another gradient", i);
   }
   if (!valid_math(math)) return fail(SU3S_EINVAL, "bad arithmetic %d", math);
   const int m = math_for(SU3S_F64, math);

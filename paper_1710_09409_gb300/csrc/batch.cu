@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(256) k_batch_tma(const BItem* __restrict__ ite
       break;
     }
     phase ^= 1;
+    ctx.gmax = p.gscal;
     read_leaves<Tree, 0, P_F64, M>(buf, lane, ctx);
     fence_proxy_async_smem();
     __syncwarp();
@@ -123,9 +124,13 @@ __global__ void __launch_bounds__(256) k_batch_tma(const BItem* __restrict__ ite
       issue_tile<Tree, P_F64, false>(lane, items[Tn.item].k, nullptr, nullptr, Tn.s0, Tn.mu, buf, bar);
 #pragma unroll
     for (int k = 0; k < (NS > 0 ? NS : 1); ++k) ctx.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
-    typename M::A acc[1][W];
-    acc_into<Tree, M, true, 1>(ctx, acc[0]);
-    store_obj<Tree::kind, P_F64, M, 1, W>(p.dst, T.s0 + lane, T.mu, acc);
+    if (M::kGuard && guard_trips<Tree>(ctx.gmax)) {
+      eval_site_f64<Tree, P_F64>(p, T.s0 + lane, T.mu);
+    } else {
+      typename M::A acc[1][W];
+      acc_into<Tree, M, true, 1>(ctx, acc[0]);
+      store_obj<Tree::kind, P_F64, M, 1, W>(p.dst, T.s0 + lane, T.mu, acc);
+    }
     T = Tn;
     i = in;
   }

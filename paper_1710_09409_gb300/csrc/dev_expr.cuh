@@ -169,6 +169,41 @@ struct LeafKind<Adj<X>, I> {
   static constexpr int value = LeafKind<X, I>::value;
 };
 
+// Degree of tree T: the most factors (leaves and real factors) in one term of
+// its expansion; it sets the range guard's bound (guard_hi).
+template <class T>
+struct Degree {
+  static constexpr int value = 1;  // leaves
+};
+template <class X, class Y>
+struct Degree<Mul<X, Y>> {
+  static constexpr int value = Degree<X>::value + Degree<Y>::value;
+};
+template <class X, class Y>
+struct Degree<Add<X, Y>> {
+  static constexpr int value = cmax(Degree<X>::value, Degree<Y>::value);
+};
+template <class X, class Y>
+struct Degree<Sub<X, Y>> {
+  static constexpr int value = cmax(Degree<X>::value, Degree<Y>::value);
+};
+template <int K, class X>
+struct Degree<Scale<K, X>> {
+  static constexpr int value = Degree<X>::value + 1;
+};
+template <class X>
+struct Degree<Adj<X>> {
+  static constexpr int value = Degree<X>::value;
+};
+
+// Whether a site whose inputs' largest high word is g must be evaluated
+// again in native FP64 (range guard of the FP64-accurate arithmetics; the
+// reverse mode of T has T's degree, dL/dZ taking the place of one factor).
+template <class T>
+__device__ __forceinline__ bool guard_trips(uint32_t g) {
+  return g >= guard_hi(Degree<T>::value);
+}
+
 // Operand view: Adj<B> is read as B with the adjoint flag set.
 template <class T>
 struct Operand {
@@ -189,6 +224,7 @@ template <class M, int NL, int NS>
 struct Ctx {
   typename M::R leaf[NL][18];
   typename M::R sc[NS > 0 ? NS : 1];
+  uint32_t gmax = 0;  // range guard: largest input high word read into this context
   template <int I, int W>
   __device__ __forceinline__ void leaf_value(typename M::R* out) const {
 #pragma unroll

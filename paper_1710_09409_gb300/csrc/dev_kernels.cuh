@@ -71,21 +71,38 @@ __device__ __forceinline__ void load_obj(const FieldDesc& f, int64_t s, int mu, 
   const int64_t b = elem_base(f, s, mu);
   if constexpr (K == KR) {
     static_assert(VPS == 1, "real fields are FP64");
-    ctx[0].leaf[slot][0] = StoreReal::template load<M>(f.ptr, b);
+    if constexpr (M::kGuard) {
+      const uint2 v = ld8((const char*)f.ptr + b * 8);
+      ctx[0].gmax = guard_max(ctx[0].gmax, v.y, v.y);
+      ctx[0].leaf[slot][0] = M::from_bits(v.x, v.y);
+    } else {
+      ctx[0].leaf[slot][0] = StoreReal::template load<M>(f.ptr, b);
+    }
     M::template normalize_obj<1>(ctx[0].leaf[slot]);
   } else {
     using St = typename BaseStore<PREC>::type;
     constexpr int NC = (K == KV) ? 3 : (IsC12<PREC>::value ? 6 : 9);
+    uint32_t gm[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       typename M::R re[VPS], im[VPS];
-      St::template load<M>(f.ptr, b + c * f.s_c, re, im);
+      if constexpr (M::kGuard) {
+        // FP64 storage, one site: the raw words also feed the range guard
+        static_assert(VPS == 1, "guarded arithmetics read FP64 storage");
+        const uint4 v = ld16((const char*)f.ptr + (b + c * f.s_c) * 16);
+        gm[c] = guard_max(0u, v.y, v.w);
+        re[0] = M::from_bits(v.x, v.y);
+        im[0] = M::from_bits(v.z, v.w);
+      } else {
+        St::template load<M>(f.ptr, b + c * f.s_c, re, im);
+      }
 #pragma unroll
       for (int v = 0; v < VPS; ++v) {
         ctx[v].leaf[slot][2 * c] = re[v];
         ctx[v].leaf[slot][2 * c + 1] = im[v];
       }
     }
+    if constexpr (M::kGuard) ctx[0].gmax = max(ctx[0].gmax, guard_reduce<NC>(gm));
     if constexpr (PREC == P_F64 || PREC == P_F64_C12) {
 #pragma unroll
       for (int v = 0; v < VPS; ++v) M::template normalize_obj<2 * NC>(ctx[v].leaf[slot]);
@@ -140,6 +157,12 @@ struct Vps<P_F64> {
 };
 
 // ------------------------------------------------------------ forward kernel
+// Native FP64 evaluation of one site from its inputs in global memory: the
+// range guard's path for sites outside the FP64-accurate arithmetics' range.
+// Kept out of line so that it costs the hot loop neither code nor registers.
+template <class Tree, int PREC>
+__device__ __noinline__ void eval_site_f64(const KParams& p, int64_t s, int mu);
+
 template <class Tree, class M, int PREC>
 __device__ __forceinline__ void eval_sites(const KParams& p, int64_t t, int mu) {
   constexpr int VPS = Vps<PREC>::value;
@@ -148,12 +171,20 @@ __device__ __forceinline__ void eval_sites(const KParams& p, int64_t t, int mu) 
   constexpr int W = Width<Tree::kind>::value;
   Ctx<M, NL, NS> ctx[VPS];
 #pragma unroll
-  for (int v = 0; v < VPS; ++v)
+  for (int v = 0; v < VPS; ++v) {
 #pragma unroll
     for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
       ctx[v].sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
+    ctx[v].gmax = p.gscal;
+  }
   const int64_t s = t * VPS;
   load_leaves<Tree, 0, PREC, M, VPS>(p, s, mu, ctx);
+  if constexpr (M::kGuard) {
+    if (guard_trips<Tree>(ctx[0].gmax)) {
+      eval_site_f64<Tree, PREC>(p, s, mu);
+      return;
+    }
+  }
   typename M::A acc[VPS][W];
 #pragma unroll
   for (int v = 0; v < VPS; ++v) {
@@ -167,6 +198,46 @@ __device__ __forceinline__ void eval_sites(const KParams& p, int64_t t, int mu) 
     }
   }
   store_obj<Tree::kind, PREC, M, VPS, W>(p.dst, s, mu, acc);
+}
+
+// Evaluation context of one site that loads each leaf from global memory
+// when the evaluation reads it (plain loads), so that only the operands in use
+// are held in registers: the range guard's native FP64 path, which runs inside
+// kernels tuned for another arithmetic and should not raise their register
+// count.
+template <class Tree, class M, int PREC>
+struct GlobalCtx {
+  static constexpr int NS = Tree::nsc;
+  const KParams* p;
+  int64_t s;
+  int mu;
+  typename M::R sc[NS > 0 ? NS : 1];
+  template <int I, int W>
+  __device__ __forceinline__ void leaf_value(typename M::R* out) const {
+    Ctx<M, 1, 0> tmp[1];
+    load_obj<LeafKind<Tree, I>::value, PREC, M, 1>(p->leaf[I], s, mu, tmp, 0);
+#pragma unroll
+    for (int r = 0; r < W; ++r) out[r] = tmp[0].leaf[0][r];
+  }
+};
+
+template <class Tree, int PREC>
+__device__ __noinline__ void eval_site_f64(const KParams& p, int64_t s, int mu) {
+  using M = MathF64;
+  constexpr int W = Width<Tree::kind>::value;
+  GlobalCtx<Tree, M, PREC> ctx{&p, s, mu};
+#pragma unroll
+  for (int k = 0; k < (Tree::nsc > 0 ? Tree::nsc : 1); ++k) ctx.sc[k] = p.sc[k];
+  typename M::A acc[1][W];
+  if constexpr (Tree::accumulates) {
+    acc_into<Tree, M, true, 1>(ctx, acc[0]);
+  } else {
+    typename M::R val[W];
+    value<Tree, M>(ctx, val);
+#pragma unroll
+    for (int r = 0; r < W; ++r) acc[0][r] = val[r];
+  }
+  store_obj<Tree::kind, PREC, M, 1, W>(p.dst, s, mu, acc);
 }
 
 // Units of work a thread (plain loads: site vectors) or a warp (staged: 32-site
@@ -221,31 +292,64 @@ __device__ __forceinline__ void store_repeated(GA& ga, Sink& sink) {
   }
 }
 
+// Native FP64 reverse mode of one site (the range guard's path; out of line).
+// It reads the leaves and dL/dZ again from global memory, so the gradient
+// fields must not overlap them (su3s_eval_adjoint checks).
+template <class Tree>
+__device__ __noinline__ void adj_site_f64(const GParams& p, int64_t s, int mu);
+
 template <class Tree, class M>
-__device__ __forceinline__ void adj_plain_range(const GParams& p, Range rg) {
+__device__ __forceinline__ void adj_site(const GParams& p, int64_t s, int mu) {
   constexpr int NL = Tree::nleaf;
   constexpr int NS = Tree::nsc;
-  constexpr int W = Width<Tree::kind>::value;
-  const int mu = blockIdx.y;
-  for (int64_t s = rg.first; s < rg.end; s += rg.stride) {
-    Ctx<M, NL, NS> ctx[1];
+  Ctx<M, NL, NS> ctx[1];
 #pragma unroll
-    for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
-      ctx[0].sc[k] = M::scalar(p.k.sc[k], p.k.sch[k], p.k.scl[k]);
-    load_leaves<Tree, 0, P_F64, M, 1>(p.k, s, mu, ctx);
-    // dL/dZ
-    Ctx<M, 1, 0> g[1];
-    load_obj<Tree::kind, P_F64, M, 1>(p.gout, s, mu, g, 0);
-    GradAcc<M, NL> ga;
-#pragma unroll
-    for (int i = 0; i < NL; ++i)
-#pragma unroll
-      for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
-    GradSink<Tree, M> sink{&p, s, mu};
-    Rev<Tree>::template run<Tree, M>(ctx[0], g[0].leaf[0], ga, sink);
-    store_repeated<Tree, 0, M>(ga, sink);
-    (void)W;
+  for (int k = 0; k < (NS > 0 ? NS : 1); ++k)
+    ctx[0].sc[k] = M::scalar(p.k.sc[k], p.k.sch[k], p.k.scl[k]);
+  ctx[0].gmax = p.k.gscal;
+  load_leaves<Tree, 0, P_F64, M, 1>(p.k, s, mu, ctx);
+  // dL/dZ
+  Ctx<M, 1, 0> g[1];
+  load_obj<Tree::kind, P_F64, M, 1>(p.gout, s, mu, g, 0);
+  if constexpr (M::kGuard) {
+    if (guard_trips<Tree>(max(ctx[0].gmax, g[0].gmax))) {
+      adj_site_f64<Tree>(p, s, mu);
+      return;
+    }
   }
+  GradAcc<M, NL> ga;
+#pragma unroll
+  for (int i = 0; i < NL; ++i)
+#pragma unroll
+    for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
+  GradSink<Tree, M> sink{&p, s, mu};
+  Rev<Tree>::template run<Tree, M>(ctx[0], g[0].leaf[0], ga, sink);
+  store_repeated<Tree, 0, M>(ga, sink);
+}
+
+template <class Tree>
+__device__ __noinline__ void adj_site_f64(const GParams& p, int64_t s, int mu) {
+  using M = MathF64;
+  constexpr int NL = Tree::nleaf;
+  GlobalCtx<Tree, M, P_F64> ctx{&p.k, s, mu};
+#pragma unroll
+  for (int k = 0; k < (Tree::nsc > 0 ? Tree::nsc : 1); ++k) ctx.sc[k] = p.k.sc[k];
+  Ctx<M, 1, 0> g[1];
+  load_obj<Tree::kind, P_F64, M, 1>(p.gout, s, mu, g, 0);
+  GradAcc<M, NL> ga;
+#pragma unroll
+  for (int i = 0; i < NL; ++i)
+#pragma unroll
+    for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
+  GradSink<Tree, M> sink{&p, s, mu};
+  Rev<Tree>::template run<Tree, M>(ctx, g[0].leaf[0], ga, sink);
+  store_repeated<Tree, 0, M>(ga, sink);
+}
+
+template <class Tree, class M>
+__device__ __forceinline__ void adj_plain_range(const GParams& p, Range rg) {
+  const int mu = blockIdx.y;
+  for (int64_t s = rg.first; s < rg.end; s += rg.stride) adj_site<Tree, M>(p, s, mu);
 }
 
 template <class Tree, class M>
@@ -340,16 +444,20 @@ template <int K, int PREC, class M, class C>
 __device__ __forceinline__ void read_obj(const unsigned char* src, int lane, C& ctx, int slot) {
   if constexpr (K == KR) {
     const uint2 v = reinterpret_cast<const uint2*>(src)[lane];
+    if constexpr (M::kGuard) ctx.gmax = guard_max(ctx.gmax, v.y, v.y);
     ctx.leaf[slot][0] = M::from_bits(v.x, v.y);
     M::template normalize_obj<1>(ctx.leaf[slot]);
   } else {
     constexpr int NC = StageBytes<K, PREC>::value / 512;
+    uint32_t gm[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const uint4 v = reinterpret_cast<const uint4*>(src + c * 512)[lane];
+      if constexpr (M::kGuard) gm[c] = guard_max(0u, v.y, v.w);
       ctx.leaf[slot][2 * c] = M::from_bits(v.x, v.y);
       ctx.leaf[slot][2 * c + 1] = M::from_bits(v.z, v.w);
     }
+    if constexpr (M::kGuard) ctx.gmax = max(ctx.gmax, guard_reduce<NC>(gm));
     M::template normalize_obj<2 * NC>(ctx.leaf[slot]);
     if constexpr (K == KM && IsC12<PREC>::value) rebuild_row2<M>(ctx.leaf[slot]);
   }
@@ -393,21 +501,26 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
       break;
     }
     phase ^= 1;
+    ctx.gmax = p.gscal;
     read_leaves<Tree, 0, PREC, M>(buf, lane, ctx);
     fence_proxy_async_smem();
     __syncwarp();
     const int64_t tn = t + wstride;
     if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, nullptr, tn << 5, mu, buf, bar);
-    typename M::A acc[1][W];
-    if constexpr (Tree::accumulates) {
-      acc_into<Tree, M, true, 1>(ctx, acc[0]);
+    if (M::kGuard && guard_trips<Tree>(ctx.gmax)) {
+      eval_site_f64<Tree, PREC>(p, (t << 5) + lane, mu);
     } else {
-      typename M::R val[W];
-      value<Tree, M>(ctx, val);
+      typename M::A acc[1][W];
+      if constexpr (Tree::accumulates) {
+        acc_into<Tree, M, true, 1>(ctx, acc[0]);
+      } else {
+        typename M::R val[W];
+        value<Tree, M>(ctx, val);
 #pragma unroll
-      for (int r = 0; r < W; ++r) acc[0][r] = M::to_acc(val[r]);
+        for (int r = 0; r < W; ++r) acc[0][r] = M::to_acc(val[r]);
+      }
+      store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + lane, mu, acc);
     }
-    store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + lane, mu, acc);
     t = tn;
   }
 }
@@ -450,6 +563,7 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
       break;
     }
     phase ^= 1;
+    ctx.gmax = p.k.gscal;
     read_leaves<Tree, 0, P_F64, M>(buf, lane, ctx);
     Ctx<M, 1, 0> g;
     read_obj<Tree::kind, P_F64, M>(buf + GOFF, lane, g, 0);
@@ -457,14 +571,18 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
     __syncwarp();
     const int64_t tn = t + wstride;
     if (tn < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, &p.tm_gout, tn << 5, mu, buf, bar);
-    GradAcc<M, NL> ga;
+    if (M::kGuard && guard_trips<Tree>(max(ctx.gmax, g.gmax))) {
+      adj_site_f64<Tree>(p, (t << 5) + lane, mu);
+    } else {
+      GradAcc<M, NL> ga;
 #pragma unroll
-    for (int i = 0; i < NL; ++i)
+      for (int i = 0; i < NL; ++i)
 #pragma unroll
-      for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
-    GradSink<Tree, M> sink{&p, (t << 5) + lane, mu};
-    Rev<Tree>::template run<Tree, M>(ctx, g.leaf[0], ga, sink);
-    store_repeated<Tree, 0, M>(ga, sink);
+        for (int r = 0; r < 18; ++r) ga.g[i][r] = M::zero();
+      GradSink<Tree, M> sink{&p, (t << 5) + lane, mu};
+      Rev<Tree>::template run<Tree, M>(ctx, g.leaf[0], ga, sink);
+      store_repeated<Tree, 0, M>(ga, sink);
+    }
     t = tn;
   }
 }
@@ -542,6 +660,7 @@ struct LazyCtx {
   uint32_t parity;
   bool has_next;
   mutable bool dead;
+  mutable uint32_t gmax;  // range guard of the current tile's site
   typename M::R sc[NS > 0 ? NS : 1];
 
   template <int I>
@@ -574,6 +693,7 @@ struct LazyCtx {
     wait_leaf<I>();
     Ctx<M, 1, 0> tmp;
     read_obj<K, PREC, M>(buf + LeafOff<Tree, PREC, I>::value, lane, tmp, 0);
+    if constexpr (M::kGuard) gmax = max(gmax, tmp.gmax);
 #pragma unroll
     for (int r = 0; r < W; ++r) out[r] = tmp.leaf[0][r];
     if constexpr (I >= NL || Reads<Tree, (I < NL ? I : 0), GRAD>::value == 1) {
@@ -654,6 +774,7 @@ __device__ __forceinline__ void lazy_range(const KParams& p, Range rg, unsigned 
     const int64_t tn = t + wstride;
     c.has_next = tn < ntiles;
     c.next_s0 = tn << 5;
+    c.gmax = p.gscal;
     typename M::A acc[1][W];
     if constexpr (Tree::accumulates) {
       acc_into<Tree, M, true, 1>(c, acc[0]);
@@ -665,7 +786,8 @@ __device__ __forceinline__ void lazy_range(const KParams& p, Range rg, unsigned 
     }
     c.template refill_repeated<0>();
     if (c.dead) break;
-    store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
+    if (M::kGuard && guard_trips<Tree>(c.gmax)) eval_site_f64<Tree, PREC>(p, (t << 5) + c.lane, c.mu);
+    else store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
     c.parity ^= 1;
     t = tn;
   }
@@ -693,6 +815,7 @@ __device__ __forceinline__ void adj_lazy_range(const GParams& p, Range rg, unsig
     const int64_t tn = t + wstride;
     c.has_next = tn < ntiles;
     c.next_s0 = tn << 5;
+    c.gmax = p.k.gscal;
     typename M::R G[W];
     c.template leaf_value<NL, W>(G);   // dL/dZ
     GradAcc<M, NL> ga;
@@ -705,6 +828,9 @@ __device__ __forceinline__ void adj_lazy_range(const GParams& p, Range rg, unsig
     store_repeated<Tree, 0, M>(ga, sink);
     c.template refill_repeated<0>();
     if (c.dead) break;
+    // leaves are read as the reverse pass needs them, so the range is known
+    // only now: a site out of range overwrites its gradients in native FP64
+    if (M::kGuard && guard_trips<Tree>(c.gmax)) adj_site_f64<Tree>(p, (t << 5) + c.lane, c.mu);
     c.parity ^= 1;
     t = tn;
   }
@@ -885,6 +1011,7 @@ struct RingCtx {
   mutable uint32_t ph;  // barrier parity of each buffer
   bool has_next;
   mutable bool dead;
+  mutable uint32_t gmax;  // range guard of the current tile's site
   typename M::R sc[NS > 0 ? NS : 1];
 
   template <int I>
@@ -921,6 +1048,7 @@ struct RingCtx {
     ph ^= 1u << b;
     Ctx<M, 1, 0> tmp;
     read_obj<K, PREC, M>(buf + b * L::BUF, lane, tmp, 0);
+    if constexpr (M::kGuard) gmax = max(gmax, tmp.gmax);
 #pragma unroll
     for (int r = 0; r < W; ++r) out[r] = tmp.leaf[0][r];
     fence_proxy_async_smem();
@@ -986,6 +1114,7 @@ __device__ __forceinline__ void ring_range(const KParams& p, Range rg, unsigned 
     c.cur_s0 = t << 5;
     c.has_next = tn < ntiles;
     c.next_s0 = tn << 5;
+    c.gmax = p.gscal;
     typename M::A acc[1][W];
     if constexpr (Tree::accumulates) {
       acc_into<Tree, M, true, 1>(c, acc[0]);
@@ -996,7 +1125,8 @@ __device__ __forceinline__ void ring_range(const KParams& p, Range rg, unsigned 
       for (int r = 0; r < W; ++r) acc[0][r] = M::to_acc(val[r]);
     }
     if (c.dead) break;
-    store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
+    if (M::kGuard && guard_trips<Tree>(c.gmax)) eval_site_f64<Tree, PREC>(p, (t << 5) + c.lane, c.mu);
+    else store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
     t = tn;
   }
   if (c.dead) c.drain();
@@ -1023,6 +1153,7 @@ __device__ __forceinline__ void adj_ring_range(const GParams& p, Range rg, unsig
     c.cur_s0 = t << 5;
     c.has_next = tn < ntiles;
     c.next_s0 = tn << 5;
+    c.gmax = p.k.gscal;
     typename M::R G[W];
     c.template leaf_value<NL, W>(G);   // dL/dZ
     GradAcc<M, NL> ga;
@@ -1034,6 +1165,8 @@ __device__ __forceinline__ void adj_ring_range(const GParams& p, Range rg, unsig
     Rev<Tree>::template run<Tree, M>(c, G, ga, sink);
     store_repeated<Tree, 0, M>(ga, sink);
     if (c.dead) break;
+    // as in the per-leaf variant: the range is known after the reverse pass
+    if (M::kGuard && guard_trips<Tree>(c.gmax)) adj_site_f64<Tree>(p, (t << 5) + c.lane, c.mu);
     t = tn;
   }
   if (c.dead) c.drain();

@@ -99,12 +99,52 @@ __device__ __forceinline__ df df_norm(float S, float lo) {
   return df{h, l};
 }
 
+// ------------------------------------------------------------ range guard
+// The FP64-accurate arithmetics hold FP64 values in narrower formats: MathDF
+// in FP32 pairs, whose exponent range ends at 2^128 (an FP64 input at or above
+// it does not split; products and sums of large inputs overflow the leading
+// parts), MathFX in integers scaled by per-object exponents (bounded results).
+// Neither represents Inf or NaN.  Kernels that evaluate in them therefore
+// keep, per site, the largest magnitude among the site's FP64 inputs (leaves,
+// dL/dZ, real factors) as the maximum of the inputs' high words with the sign
+// cleared: non-negative FP64 values order as their bit patterns, and Inf and
+// NaN come after every finite value.  A site whose maximum reaches its tree's
+// bound 2^t(d) is evaluated again in native FP64 from its inputs in global
+// memory, before anything of it is stored, so every input gets the IEEE
+// result (NaN, Inf, values beyond FP32 range).  d is the tree's degree (the
+// most factors, leaves and real factors, in one product term); with
+// t(d) = floor((120 - 3 (d - 1)) / d) every term, partial sum and TwoSum
+// intermediate of a site in range stays below 2^127 (a 3x3 complex product
+// term sums at most 6 |x||y| per real; a degree-3 term at most 36 of them).
+// Magnitudes below 2^-126 are not guarded: MathDF flushes them, an absolute
+// error below 2^-126 times the other factors' magnitudes.
+__host__ __device__ constexpr uint32_t guard_hi(int degree) {
+  return (uint32_t)(1023 + (120 - 3 * (degree - 1)) / degree) << 20;
+}
+
+// running maximum of two inputs' high words (sign bits cleared)
+__device__ __forceinline__ uint32_t guard_max(uint32_t g, uint32_t hi_a, uint32_t hi_b) {
+  return __vimax3_u32(g, hi_a & 0x7FFFFFFFu, hi_b & 0x7FFFFFFFu);
+}
+
+// maximum of N per-element guard words by a pairwise tree (depth log2 N, so
+// it completes as soon as the object is read)
+template <int N>
+__device__ __forceinline__ uint32_t guard_reduce(uint32_t* g) {
+#pragma unroll
+  for (int w = 1; w < N; w *= 2)
+#pragma unroll
+    for (int i = 0; i + w < N; i += 2 * w) g[i] = max(g[i], g[i + w]);
+  return g[0];
+}
+
 // ------------------------------------------------------------- MathF64
 struct MathF64 {
   using R = double;   // one real component
   using A = double;   // accumulator
   static constexpr bool kScaled = false;  // every term shares one scale
   static constexpr bool kPaired = false;  // no packed (re, im) products
+  static constexpr bool kGuard = false;   // IEEE semantics for every input
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return __hiloint2double((int)hi, (int)lo);
   }
@@ -145,6 +185,7 @@ struct MathDF {
   using A = DAcc;
   static constexpr bool kScaled = false;
   static constexpr bool kPaired = true;   // complex products in packed (re, im) lanes
+  static constexpr bool kGuard = true;    // FP32 exponent range: sites are range-checked
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return df_split_bits(lo, hi);
   }
@@ -367,6 +408,7 @@ struct MathFX {
   using A = FAcc;
   static constexpr bool kScaled = true;  // terms of different objects differ in scale
   static constexpr bool kPaired = false;
+  static constexpr bool kGuard = true;   // finite inputs of bounded scale: range-checked
 
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return fxr{(int)hi, (int)lo, 0};
@@ -507,6 +549,7 @@ struct MathF32 {
   using A = float;
   static constexpr bool kScaled = false;
   static constexpr bool kPaired = false;
+  static constexpr bool kGuard = false;
   __device__ static __forceinline__ R finish(const A& a) { return a; }
   __device__ static __forceinline__ A to_acc(const R& x) { return x; }
   __device__ static __forceinline__ A zero() { return 0.0f; }

@@ -58,19 +58,23 @@ struct IRegs {
   }
 };
 
-// Object of W reals of field f (FP64 storage) at site s, link mu.
+// Object of W reals of field f (FP64 storage) at site s, link mu; g is the
+// site's range guard (largest input high word, see dev_math.cuh).
 template <class M, int W>
-__device__ __forceinline__ void i_load(const FieldDesc& f, int64_t s, int mu, typename M::R* r) {
+__device__ __forceinline__ void i_load(const FieldDesc& f, int64_t s, int mu, typename M::R* r,
+                                       uint32_t& g) {
   const int64_t b = elem_base(f, s, mu);
   if constexpr (W == 1) {
-    r[0] = StoreReal::template load<M>(f.ptr, b);
+    const uint2 v = ld8((const char*)f.ptr + b * 8);
+    if constexpr (M::kGuard) g = guard_max(g, v.y, v.y);
+    r[0] = M::from_bits(v.x, v.y);
   } else {
 #pragma unroll
     for (int c = 0; c < W / 2; ++c) {
-      typename M::R re[1], im[1];
-      Store<P_F64>::template load<M>(f.ptr, b + c * f.s_c, re, im);
-      r[2 * c] = re[0];
-      r[2 * c + 1] = im[0];
+      const uint4 v = ld16((const char*)f.ptr + (b + c * f.s_c) * 16);
+      if constexpr (M::kGuard) g = guard_max(g, v.y, v.w);
+      r[2 * c] = M::from_bits(v.x, v.y);
+      r[2 * c + 1] = M::from_bits(v.z, v.w);
     }
   }
   M::template normalize_obj<W>(r);
@@ -121,89 +125,116 @@ __device__ __forceinline__ void i_store(const FieldDesc& dst, int64_t s, int mu,
   }
 }
 
+// Run the program on site s into the register file R (g: range guard).
+template <class M>
+__device__ __forceinline__ void i_run(const KParams& p, const IProg& prog, const IRegs<M>& R,
+                                      int64_t s, int mu, uint32_t& g) {
+  using Rv = typename M::R;
+  using Av = typename M::A;
+  for (int pc = 0; pc < prog.n; ++pc) {
+    const IIns in = prog.ins[pc];
+    switch (in.op) {
+      case I_LOAD: {
+        Rv v[18];
+        if (in.w == 18) {
+          i_load<M, 18>(p.leaf[in.arg], s, mu, v, g);
+          R.template put<18>(in.dst, v);
+        } else if (in.w == 6) {
+          i_load<M, 6>(p.leaf[in.arg], s, mu, v, g);
+          R.template put<6>(in.dst, v);
+        } else {
+          i_load<M, 1>(p.leaf[in.arg], s, mu, v, g);
+          R.template put<1>(in.dst, v);
+        }
+        break;
+      }
+      case I_MMUL: {
+        Rv x[18], y[18], d[18];
+        Av acc[18];
+        R.template get<18>(in.a, x);
+        R.template get<18>(in.b, y);
+        mm_acc<M, true, 1, false, false>(acc, x, y);
+        finish<M, 18>(d, acc);
+        R.template put<18>(in.dst, d);
+        break;
+      }
+      case I_MVMUL: {
+        Rv x[18], y[6], d[6];
+        Av acc[6];
+        R.template get<18>(in.a, x);
+        R.template get<6>(in.b, y);
+        mv_acc<M, true, 1, false>(acc, x, y);
+        finish<M, 6>(d, acc);
+        R.template put<6>(in.dst, d);
+        break;
+      }
+      case I_RMUL: {
+        Rv x[1], y[1], d[1];
+        Av acc[1];
+        R.template get<1>(in.a, x);
+        R.template get<1>(in.b, y);
+        M::template fma<true, 1>(acc[0], x[0], y[0]);
+        finish<M, 1>(d, acc);
+        R.template put<1>(in.dst, d);
+        break;
+      }
+      case I_ADD:
+      case I_SUB: {
+        const int sg = in.op == I_ADD ? 1 : -1;
+        if (in.w == 18) i_add<M, 18>(R, in, sg);
+        else if (in.w == 6) i_add<M, 6>(R, in, sg);
+        else i_add<M, 1>(R, in, sg);
+        break;
+      }
+      case I_SCALE: {
+        if (in.w == 18) i_scale<M, 18>(R, in, p);
+        else if (in.w == 6) i_scale<M, 6>(R, in, p);
+        else i_scale<M, 1>(R, in, p);
+        break;
+      }
+      default: {  // I_ADJ
+        Rv x[18], t[18];
+        R.template get<18>(in.a, x);
+        adjoint<M>(t, x);
+        R.template put<18>(in.dst, t);
+        break;
+      }
+    }
+  }
+}
+
+template <class M>
+__device__ __forceinline__ void i_store_root(const KParams& p, const IProg& prog, const IRegs<M>& R,
+                                             int64_t s, int mu) {
+  if (prog.root_kind == KR) i_store<M, 1>(p.dst, s, mu, R, prog.root);
+  else if (prog.root_kind == KV) i_store<M, 6>(p.dst, s, mu, R, prog.root);
+  else i_store<M, 18>(p.dst, s, mu, R, prog.root);
+}
+
+// The range guard's path: the program again in native FP64 on this thread's
+// slice of the register file (a double is no wider than any arithmetic's
+// real, so it fits), then the store.  Out of line, off the hot loop.
+__device__ __noinline__ void i_site_f64(const KParams& p, const IProg& prog, void* base, int nt,
+                                        int tid, int64_t s, int mu) {
+  const IRegs<MathF64> R{reinterpret_cast<double*>(base), nt, tid};
+  uint32_t g = 0;
+  i_run<MathF64>(p, prog, R, s, mu, g);
+  i_store_root<MathF64>(p, prog, R, s, mu);
+}
+
 template <class M>
 __global__ void __launch_bounds__(128) k_interp(const __grid_constant__ KParams p,
                                                 const __grid_constant__ IProg prog) {
   using Rv = typename M::R;
-  using Av = typename M::A;
   extern __shared__ __align__(16) unsigned char i_smem[];
   const IRegs<M> R{reinterpret_cast<Rv*>(i_smem), (int)blockDim.x, (int)threadIdx.x};
   const int mu = blockIdx.y;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.nvec; s += stride) {
-    for (int pc = 0; pc < prog.n; ++pc) {
-      const IIns in = prog.ins[pc];
-      switch (in.op) {
-        case I_LOAD: {
-          Rv v[18];
-          if (in.w == 18) {
-            i_load<M, 18>(p.leaf[in.arg], s, mu, v);
-            R.template put<18>(in.dst, v);
-          } else if (in.w == 6) {
-            i_load<M, 6>(p.leaf[in.arg], s, mu, v);
-            R.template put<6>(in.dst, v);
-          } else {
-            i_load<M, 1>(p.leaf[in.arg], s, mu, v);
-            R.template put<1>(in.dst, v);
-          }
-          break;
-        }
-        case I_MMUL: {
-          Rv x[18], y[18], d[18];
-          Av acc[18];
-          R.template get<18>(in.a, x);
-          R.template get<18>(in.b, y);
-          mm_acc<M, true, 1, false, false>(acc, x, y);
-          finish<M, 18>(d, acc);
-          R.template put<18>(in.dst, d);
-          break;
-        }
-        case I_MVMUL: {
-          Rv x[18], y[6], d[6];
-          Av acc[6];
-          R.template get<18>(in.a, x);
-          R.template get<6>(in.b, y);
-          mv_acc<M, true, 1, false>(acc, x, y);
-          finish<M, 6>(d, acc);
-          R.template put<6>(in.dst, d);
-          break;
-        }
-        case I_RMUL: {
-          Rv x[1], y[1], d[1];
-          Av acc[1];
-          R.template get<1>(in.a, x);
-          R.template get<1>(in.b, y);
-          M::template fma<true, 1>(acc[0], x[0], y[0]);
-          finish<M, 1>(d, acc);
-          R.template put<1>(in.dst, d);
-          break;
-        }
-        case I_ADD:
-        case I_SUB: {
-          const int sg = in.op == I_ADD ? 1 : -1;
-          if (in.w == 18) i_add<M, 18>(R, in, sg);
-          else if (in.w == 6) i_add<M, 6>(R, in, sg);
-          else i_add<M, 1>(R, in, sg);
-          break;
-        }
-        case I_SCALE: {
-          if (in.w == 18) i_scale<M, 18>(R, in, p);
-          else if (in.w == 6) i_scale<M, 6>(R, in, p);
-          else i_scale<M, 1>(R, in, p);
-          break;
-        }
-        default: {  // I_ADJ
-          Rv x[18], t[18];
-          R.template get<18>(in.a, x);
-          adjoint<M>(t, x);
-          R.template put<18>(in.dst, t);
-          break;
-        }
-      }
-    }
-    if (prog.root_kind == KR) i_store<M, 1>(p.dst, s, mu, R, prog.root);
-    else if (prog.root_kind == KV) i_store<M, 6>(p.dst, s, mu, R, prog.root);
-    else i_store<M, 18>(p.dst, s, mu, R, prog.root);
+    uint32_t g = p.gscal;
+    i_run<M>(p, prog, R, s, mu, g);
+    if (M::kGuard && g >= p.ghi) i_site_f64(p, prog, i_smem, (int)blockDim.x, (int)threadIdx.x, s, mu);
+    else i_store_root<M>(p, prog, R, s, mu);
   }
 }
 
@@ -306,6 +337,8 @@ struct Builder {
 
 template <class M>
 cudaError_t launch_interp(const KParams& p, const IProg& prog, cudaStream_t st) {
+  static_assert(!M::kGuard || sizeof(typename M::R) >= sizeof(double),
+                "the range guard reruns the program in FP64 on the same register file");
   // shared memory: nregs registers of 18 reals per thread; 128 threads per
   // block while that fits in 200 KB, fewer for long programs
   const size_t per_thread = (size_t)prog.nregs * 18 * sizeof(typename M::R);
@@ -327,6 +360,21 @@ cudaError_t launch_interp(const KParams& p, const IProg& prog, cudaStream_t st) 
 }
 }  // namespace
 
+// Degree of a runtime tree (most factors in one term), as Degree<> of the
+// compiled trees: it sets the range guard's bound.
+static int degree(const su3s_expr* e) {
+  switch (e->op) {
+    case 0: return 1;
+    case 1: return degree(e->a) + degree(e->b);
+    case 4: return degree(e->a) + 1;
+    case 5: return degree(e->a);
+    default: {
+      const int a = degree(e->a), b = degree(e->b);
+      return a > b ? a : b;
+    }
+  }
+}
+
 int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, cudaStream_t st) {
   Builder bld;
   memset(&bld.prog, 0, sizeof bld.prog);
@@ -341,6 +389,7 @@ int interp_eval(const su3s_expr* e, const Canon& c, su3s_field* dest, int math, 
   bld.prog.root_kind = c.kind;
   KParams p;
   build_params(c, dest, 1, &p);
+  p.ghi = guard_hi(degree(e));
   cudaError_t ce = math == MATH_F64  ? launch_interp<MathF64>(p, bld.prog, st)
                    : math == MATH_FX ? launch_interp<MathFX>(p, bld.prog, st)
                                      : launch_interp<MathDFScalar>(p, bld.prog, st);

@@ -42,6 +42,8 @@ struct KParams {
   float scl[kMaxScalars];
   int64_t nvec;             // site vectors per link (= Vpad / sites per vector)
   int32_t nmu;
+  uint32_t gscal;           // range guard: largest high word (sign cleared) of the real factors
+  uint32_t ghi;             // range guard bound of the interpreter's program (guard_hi)
   int* err;                 // device error word (bounded waits that gave up), may be null
 };
 
