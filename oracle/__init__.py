@@ -18,6 +18,10 @@ for the definitions):
   cshift          Sec. 6 (Cshift): circular shift along one lattice direction
   hop             Sec. 6 (Dslash): colour part of the nearest-neighbour
                   hopping term, sum_mu U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu)
+  dslash          Sec. 6 (Dslash): the Wilson hopping term with its spin
+                  structure, sum_mu (1 - g_mu) U_mu(x) psi(x+mu)
+                  + (1 + g_mu) U_mu(x-mu)^dagger psi(x-mu) on spinor fields
+  gamma           the Euclidean gamma matrices (chiral basis) dslash uses
 
 Parity status: every function here is pinned by the CPU tests in
 tests/test_oracle.py (brute force against numpy/torch, closed forms,
@@ -78,6 +82,10 @@ def _bind(lib):
     lib.oracle_cshift.restype = None
     lib.oracle_hop.argtypes = [P, P, P, P, ctypes.c_int]
     lib.oracle_hop.restype = None
+    lib.oracle_dslash.argtypes = [P, P, P, P, ctypes.c_int]
+    lib.oracle_dslash.restype = None
+    lib.oracle_gamma.argtypes = [ctypes.c_int, P]
+    lib.oracle_gamma.restype = ctypes.c_int
     return lib
 
 
@@ -276,4 +284,26 @@ def hop(u, x, dims):
     kind = {(3, 3, 2): 0, (3, 2): 1}[x.shape[1:]]
     out = np.empty_like(x)
     _load().oracle_hop(u.ctypes.data, x.ctypes.data, out.ctypes.data, _dims(dims), kind)
+    return out
+
+
+def gamma(mu):
+    """gamma_mu (mu = 0..3, directions x, y, z, t) or gamma_5 (mu = 4) of the
+    chiral basis dslash uses, as a complex (4, 4) array."""
+    out = np.empty((4, 4, 2))
+    if _load().oracle_gamma(int(mu), out.ctypes.data) != 0:
+        raise ValueError(mu)
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def dslash(u, psi, dims, r=1):
+    """out(s) = sum_mu (1 - r g_mu) U_mu(s) psi(s+mu) + (1 + r g_mu) U_mu(s-mu)^dagger psi(s-mu):
+    the Wilson hopping term with spin (Sec. 6; r = 1 is the operator, r = -1
+    swaps the projectors).  u: (V*4, 3, 3, 2) links; psi: (V*4, 3, 2) or
+    (V, 4, 3, 2) spinors (spin s of site x at row 4x + s)."""
+    u, psi = _c(u), _c(psi)
+    v = int(np.prod(dims))
+    assert u.shape == (4 * v, 3, 3, 2) and psi.size == 24 * v
+    out = np.empty_like(psi)
+    _load().oracle_dslash(u.ctypes.data, psi.ctypes.data, out.ctypes.data, _dims(dims), int(r))
     return out

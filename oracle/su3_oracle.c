@@ -43,6 +43,18 @@
  *                  v a colour vector or a colour matrix field, U the 4 links.
  *                  Site order: s = x + Lx*(y + Ly*(z + Lz*t)); directions
  *                  0..3 = x, y, z, t.
+ *   oracle_dslash  the Wilson Dslash hopping term with its spin structure, the
+ *                  operator whose port the paper names as its next step
+ *                  (Sec. 6):
+ *                  out(x) = sum_mu [ (1 - r gamma_mu) (x) U_mu(x) psi(x+mu)
+ *                                  + (1 + r gamma_mu) (x) U_mu(x-mu)^dagger psi(x-mu) ],
+ *                  psi a spinor field double[V][4][3][2] (spin, colour,
+ *                  re/im), r = +1 for the operator (r = -1 swaps the two
+ *                  projectors; the sum of both is twice the colour hopping
+ *                  term on every spin).  Written as the plain definition: the
+ *                  full 4x4 spin matrix (1 -+ r gamma_mu) applied to U psi.
+ *                  Euclidean gamma matrices of the chiral basis,
+ *                  gamma_5 = diag(1, 1, -1, -1) (oracle_gamma returns them).
  */
 #include <math.h>
 #include <stdint.h>
@@ -466,6 +478,79 @@ void oracle_hop(const double* U, const double* v, double* out, const int* L, int
             if (kind == OR_MATRIX) mat_mul(a, v + w * bw, t);
             else mat_vec(a, v + w * bw, t);
             for (int r = 0; r < w; ++r) o[r] += t[r];
+        }
+    }
+}
+
+/* ---------- the Wilson hopping term with spin ---------- */
+
+/* Euclidean gamma matrices, chiral basis: gamma_mu = [[0, s_mu], [s_mu^+, 0]]
+ * in 2x2 spin blocks, s_x = [[0, i], [i, 0]], s_y = [[0, -1], [1, 0]],
+ * s_z = [[i, 0], [0, -i]], s_t = identity; entry [mu][row][col][re/im].
+ * Index 4 is gamma_5 = diag(1, 1, -1, -1). */
+static const double GAMMA[5][4][4][2] = {
+    {{{0, 0}, {0, 0}, {0, 0}, {0, 1}},
+     {{0, 0}, {0, 0}, {0, 1}, {0, 0}},
+     {{0, 0}, {0, -1}, {0, 0}, {0, 0}},
+     {{0, -1}, {0, 0}, {0, 0}, {0, 0}}},
+    {{{0, 0}, {0, 0}, {0, 0}, {-1, 0}},
+     {{0, 0}, {0, 0}, {1, 0}, {0, 0}},
+     {{0, 0}, {1, 0}, {0, 0}, {0, 0}},
+     {{-1, 0}, {0, 0}, {0, 0}, {0, 0}}},
+    {{{0, 0}, {0, 0}, {0, 1}, {0, 0}},
+     {{0, 0}, {0, 0}, {0, 0}, {0, -1}},
+     {{0, -1}, {0, 0}, {0, 0}, {0, 0}},
+     {{0, 0}, {0, 1}, {0, 0}, {0, 0}}},
+    {{{0, 0}, {0, 0}, {1, 0}, {0, 0}},
+     {{0, 0}, {0, 0}, {0, 0}, {1, 0}},
+     {{1, 0}, {0, 0}, {0, 0}, {0, 0}},
+     {{0, 0}, {1, 0}, {0, 0}, {0, 0}}},
+    {{{1, 0}, {0, 0}, {0, 0}, {0, 0}},
+     {{0, 0}, {1, 0}, {0, 0}, {0, 0}},
+     {{0, 0}, {0, 0}, {-1, 0}, {0, 0}},
+     {{0, 0}, {0, 0}, {0, 0}, {-1, 0}}},
+};
+
+/* gamma_mu (mu = 0..3) or gamma_5 (mu = 4) as double[4][4][2]; -1 for a bad mu. */
+int oracle_gamma(int mu, double* out) {
+    if (mu < 0 || mu > 4) return -1;
+    memcpy(out, GAMMA[mu], sizeof GAMMA[mu]);
+    return 0;
+}
+
+/* o (spinor, 24 doubles) += P chi, P = 1 + sg * r * gamma_mu (4x4 complex),
+ * chi[s] = the colour vector of spin s (already multiplied by the link). */
+static void spin_project_add(double* o, const double chi[4][6], int mu, double sgr) {
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            double pr = sgr * GAMMA[mu][a][b][0], pi = sgr * GAMMA[mu][a][b][1];
+            if (a == b) pr += 1.0;
+            for (int c = 0; c < 3; ++c) {
+                double xr = chi[b][2 * c], xi = chi[b][2 * c + 1];
+                o[6 * a + 2 * c] += pr * xr;
+                o[6 * a + 2 * c] -= pi * xi;
+                o[6 * a + 2 * c + 1] += pr * xi;
+                o[6 * a + 2 * c + 1] += pi * xr;
+            }
+        }
+}
+
+/* out(x) = sum_mu (1 - r g_mu) U_mu(x) psi(x+mu) + (1 + r g_mu) U_mu(x-mu)^+ psi(x-mu);
+ * U: double[V][4][3][3][2]; psi, out: double[V][4][3][2]. */
+void oracle_dslash(const double* U, const double* psi, double* out, const int* L, int r) {
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    double chi[4][6], a[18];
+    for (int64_t s = 0; s < V; ++s) {
+        double* o = out + 24 * s;
+        for (int k = 0; k < 24; ++k) o[k] = 0.0;
+        for (int mu = 0; mu < 4; ++mu) {
+            const int64_t fw = shifted_site(s, L, mu, +1);
+            const int64_t bw = shifted_site(s, L, mu, -1);
+            for (int sp = 0; sp < 4; ++sp) mat_vec(U + 18 * (4 * s + mu), psi + 24 * fw + 6 * sp, chi[sp]);
+            spin_project_add(o, (const double(*)[6])chi, mu, -(double)r);
+            mat_adj(U + 18 * (4 * bw + mu), a);
+            for (int sp = 0; sp < 4; ++sp) mat_vec(a, psi + 24 * bw + 6 * sp, chi[sp]);
+            spin_project_add(o, (const double(*)[6])chi, mu, (double)r);
         }
     }
 }

@@ -504,3 +504,94 @@ def test_hop_gauge_covariance():
     up = np.stack([Up.real, Up.imag], -1).reshape(4 * v, 3, 3, 2)
     hp = oracle.hop(up, np.stack([xp.real, xp.imag], -1), dims)
     assert np.abs(cplx(hp) - G @ cplx(oracle.hop(u, x, dims))).max() < 1e-13
+
+
+# ------------------------------------ Wilson hopping term with spin (Sec. 6)
+def spinor(seed, field, v):
+    """Gaussian spinor field: 4 spin components of a colour vector per site."""
+    return synth.gauss_vector(seed, field, 4 * v).reshape(v, 4, 3, 2)
+
+
+def test_gamma_matrices_form_the_euclidean_clifford_algebra():
+    g = [oracle.gamma(mu) for mu in range(4)]
+    g5 = oracle.gamma(4)
+    eye = np.eye(4)
+    for a in range(4):
+        assert np.array_equal(g[a], np.conj(g[a].T))             # hermitian
+        for b in range(4):
+            assert np.array_equal(g[a] @ g[b] + g[b] @ g[a], 2.0 * eye * (a == b))
+        assert np.array_equal(g[a] @ g5 + g5 @ g[a], np.zeros((4, 4)))
+    assert np.array_equal(g[0] @ g[1] @ g[2] @ g[3], g5)
+    assert np.array_equal(g5, np.diag([1, 1, -1, -1]))           # chiral basis
+    for a in range(4):                                           # (1 -+ g)/2: rank-2 projectors
+        for sg in (1, -1):
+            p = 0.5 * (eye + sg * g[a])
+            assert np.array_equal(p @ p, p) and np.linalg.matrix_rank(p) == 2
+
+
+@pytest.mark.parametrize("dims", STENCIL_DIMS)
+def test_dslash_projector_sum_is_twice_the_colour_hopping_term(dims):
+    # (1 - g) + (1 + g) = 2: the operator plus its projector-swapped form is
+    # twice the colour hopping term, applied to each spin component
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    psi = spinor(SEED, 4, v)
+    both = oracle.dslash(u, psi, dims, 1) + oracle.dslash(u, psi, dims, -1)
+    hop = np.stack([oracle.hop(u, np.ascontiguousarray(psi[:, s]), dims) for s in range(4)], 1)
+    assert np.abs(both - 2.0 * hop).max() < 1e-13
+
+
+def test_dslash_is_gamma5_hermitian():
+    # <a, D b> = <g5 D g5 a, b>: the hopping term's adjoint is g5 D g5
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    a, b = spinor(SEED, 4, v), spinor(SEED + 1, 4, v)
+    g5 = np.array([1.0, 1.0, -1.0, -1.0])[None, :, None, None]
+    lhs = np.vdot(cplx(a), cplx(oracle.dslash(u, b, dims)))
+    rhs = np.vdot(cplx(g5 * oracle.dslash(u, g5 * a, dims)), cplx(b))
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+    # and it is not hermitian itself (the projectors do not commute with g5)
+    rhs_h = np.vdot(cplx(oracle.dslash(u, a, dims)), cplx(b))
+    assert abs(lhs - rhs_h) > 1e-3 * abs(lhs)
+
+
+def test_dslash_gauge_covariance():
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    psi = spinor(SEED, 4, v)
+    g = synth.su3(SEED + 9, 2, v)
+    G, U = cplx(g), cplx(u).reshape(v, 4, 3, 3)
+    Up = np.empty_like(U)
+    for mu in range(4):
+        gn = cplx(oracle.cshift(g, dims, mu, 1))
+        Up[:, mu] = G @ U[:, mu] @ np.conj(np.swapaxes(gn, -1, -2))
+    up = np.stack([Up.real, Up.imag], -1).reshape(4 * v, 3, 3, 2)
+    pp = np.einsum("nij,nsj->nsi", G, cplx(psi))
+    out_p = oracle.dslash(up, np.stack([pp.real, pp.imag], -1), dims)
+    ref = np.einsum("nij,nsj->nsi", G, cplx(oracle.dslash(u, psi, dims)))
+    assert np.abs(cplx(out_p) - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 2, 5), (2, 2, 2, 2)])
+def test_dslash_free_field_plane_wave(dims):
+    # unit links, psi(x) = exp(i p.x) u: D psi = sum_mu [(1 - g_mu) e^{i p_mu}
+    # + (1 + g_mu) e^{-i p_mu}] psi, a 4x4 matrix in spin space only
+    v = synth.volume(dims)
+    links = np.zeros((4 * v, 3, 3, 2))
+    links[:, [0, 1, 2], [0, 1, 2], 0] = 1.0
+    n = np.array([1, 2, 1, 3])
+    p = 2 * np.pi * n / np.array(dims)
+    x = np.stack(np.meshgrid(*[np.arange(L) for L in dims], indexing="ij"), -1)
+    x = x.transpose(3, 2, 1, 0, 4).reshape(v, 4)                # site order x fastest
+    phase = np.exp(1j * (x @ p))
+    rng = np.random.default_rng(7)
+    u0 = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+    psi = phase[:, None, None] * u0[None]
+    eye = np.eye(4)
+    m = sum((eye - oracle.gamma(mu)) * np.exp(1j * p[mu]) + (eye + oracle.gamma(mu)) * np.exp(-1j * p[mu])
+            for mu in range(4))
+    ref = phase[:, None, None] * (m @ u0)[None]
+    got = cplx(oracle.dslash(links, np.stack([psi.real, psi.imag], -1), dims))
+    assert np.abs(got - ref).max() < 1e-13

@@ -90,6 +90,52 @@ def pin_hop_hermitian():
     return abs(lhs - rhs) <= 1e-13 * abs(lhs)
 
 
+def pin_dslash_gamma5_hermitian():
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    a = synth.gauss_vector(SEED, 4, 4 * v).reshape(v, 4, 3, 2)
+    b = synth.gauss_vector(SEED + 1, 4, 4 * v).reshape(v, 4, 3, 2)
+    g5 = np.array([1.0, 1.0, -1.0, -1.0])[None, :, None, None]
+    lhs = np.vdot(cplx(a), cplx(oracle.dslash(u, b, dims)))
+    rhs = np.vdot(cplx(g5 * oracle.dslash(u, g5 * a, dims)), cplx(b))
+    return abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def pin_dslash_projector_sum():
+    dims = (3, 2, 5, 4)
+    v = synth.volume(dims)
+    u = synth.su3(SEED, 0, 4 * v)
+    psi = synth.gauss_vector(SEED, 4, 4 * v).reshape(v, 4, 3, 2)
+    both = oracle.dslash(u, psi, dims, 1) + oracle.dslash(u, psi, dims, -1)
+    hop = np.stack([oracle.hop(u, np.ascontiguousarray(psi[:, s]), dims) for s in range(4)], 1)
+    return np.abs(both - 2.0 * hop).max() < 1e-13
+
+
+def pin_dslash_plane_wave():
+    dims = (4, 3, 2, 5)
+    v = synth.volume(dims)
+    links = np.zeros((4 * v, 3, 3, 2))
+    links[:, [0, 1, 2], [0, 1, 2], 0] = 1.0
+    p = 2 * np.pi * np.array([1, 2, 1, 3]) / np.array(dims)
+    x = np.stack(np.meshgrid(*[np.arange(L) for L in dims], indexing="ij"), -1)
+    x = x.transpose(3, 2, 1, 0, 4).reshape(v, 4)
+    phase = np.exp(1j * (x @ p))
+    u0 = np.arange(12).reshape(4, 3) + 0.5j
+    psi = phase[:, None, None] * u0[None]
+    # the closed form with the gamma matrices written out here (chiral basis)
+    i = 1j
+    g = [np.array([[0, 0, 0, i], [0, 0, i, 0], [0, -i, 0, 0], [-i, 0, 0, 0]]),
+         np.array([[0, 0, 0, -1], [0, 0, 1, 0], [0, 1, 0, 0], [-1, 0, 0, 0]]),
+         np.array([[0, 0, i, 0], [0, 0, 0, -i], [-i, 0, 0, 0], [0, i, 0, 0]]),
+         np.array([[0, 0, 1, 0], [0, 0, 0, 1], [1, 0, 0, 0], [0, 1, 0, 0]])]
+    m = sum((np.eye(4) - g[mu]) * np.exp(1j * p[mu]) + (np.eye(4) + g[mu]) * np.exp(-1j * p[mu])
+            for mu in range(4))
+    ref = phase[:, None, None] * (m @ u0)[None]
+    got = cplx(oracle.dslash(links, np.stack([psi.real, psi.imag], -1), dims))
+    return np.abs(got - ref).max() < 1e-12
+
+
 MUTATIONS = [
     ("mm sign", "re -= xi * yi;", "re += xi * yi;", pin_mm_brute_force),
     ("mm transposed operand", "double yr = y[2 * (3 * j + k)], yi = y[2 * (3 * j + k) + 1];",
@@ -113,10 +159,18 @@ MUTATIONS = [
      pin_reunitarize_det),
     ("cshift wrong direction", "int64_t m = ((c[dim] + shift) % L[dim] + L[dim]) % L[dim];",
      "int64_t m = ((c[dim] - shift) % L[dim] + L[dim]) % L[dim];", pin_cshift_roll),
-    ("hop backward link not daggered", "mat_adj(U + 18 * (4 * bw + mu), a);",
-     "memcpy(a, U + 18 * (4 * bw + mu), sizeof a);", pin_hop_hermitian),
-    ("hop backward link at the site", "mat_adj(U + 18 * (4 * bw + mu), a);",
-     "mat_adj(U + 18 * (4 * s + mu), a);", pin_hop_hermitian),
+    ("hop backward link not daggered", "mat_adj(U + 18 * (4 * bw + mu), a);\n            if (kind",
+     "memcpy(a, U + 18 * (4 * bw + mu), sizeof a);\n            if (kind", pin_hop_hermitian),
+    ("hop backward link at the site", "mat_adj(U + 18 * (4 * bw + mu), a);\n            if (kind",
+     "mat_adj(U + 18 * (4 * s + mu), a);\n            if (kind", pin_hop_hermitian),
+    ("dslash projectors swapped", "spin_project_add(o, (const double(*)[6])chi, mu, -(double)r);",
+     "spin_project_add(o, (const double(*)[6])chi, mu, (double)r);", pin_dslash_gamma5_hermitian),
+    ("dslash gamma_y entry sign", "{{0, 0}, {0, 0}, {0, 0}, {-1, 0}},",
+     "{{0, 0}, {0, 0}, {0, 0}, {1, 0}},", pin_dslash_plane_wave),
+    ("dslash imaginary part of the projector dropped", "                o[6 * a + 2 * c] -= pi * xi;\n",
+     "\n", pin_dslash_plane_wave),
+    ("dslash backward link not daggered", "mat_adj(U + 18 * (4 * bw + mu), a);\n            for (int sp",
+     "memcpy(a, U + 18 * (4 * bw + mu), sizeof a);\n            for (int sp", pin_dslash_projector_sum),
 ]
 
 
