@@ -776,6 +776,20 @@ def run_studies(su3s, synth, torch, stream, which):
                                 "GB_s": round(bsite * v / ms / 1e6, 1),
                                 "Gsites_s": round(v / ms / 1e6, 3)})
                 del X, Z
+            # the Wilson hopping term with spin: spinors are vector fields with
+            # 4 spin components; 4 links 576 B + spinor 192 B + output 192 B,
+            # 1320 flops per site
+            P = fld(lat, su3s.VECTOR, 4, F64, synth.gauss_vector(SEED + 6, 5, 4 * v))
+            Q = P.like()
+            for mname in MATH_NAMES:
+                ms = _time_ms(torch, stream,
+                              lambda: su3s.dslash(Q, U, P, MATH_IDS[mname], stream))
+                out.append({"study": "stencil", "op": "wilson dslash (spin)", "lattice": list(dims),
+                            "math": mname, "ms": round(ms, 5), "B_per_site": 960,
+                            "GB_s": round(960 * v / ms / 1e6, 1),
+                            "Gsites_s": round(v / ms / 1e6, 3),
+                            "GFLOP_s": round(1320 * v / ms / 1e6, 1)})
+            del P, Q
             A = fld(lat, MAT, 1, F64, synth.su3(SEED + 6, 2, v))
             B = A.like()
             for dim in (0, 3):
@@ -784,6 +798,39 @@ def run_studies(su3s, synth, torch, stream, which):
                             "lattice": list(dims), "ms": round(ms, 5), "B_per_site": 288,
                             "GB_s": round(288 * v / ms / 1e6, 1)})
             del U, A, B
+            torch.cuda.empty_cache()
+
+    if "blocks" in which:
+        # the vector-length / block-shape study of Sec. 5 (Fig. 4 and the 2-d
+        # block): z = a*b at 48^4, GB/s against threads per CTA (32-site tiles,
+        # i.e. warps, per CTA: the 2-d block's y extent) and CTAs per SM, for
+        # the staged and plain-load kernels in FP64 storage (pair arithmetic)
+        # and the plain-load kernel in FP32 storage (the paper's single
+        # precision).  A CTA of more than 256 threads cannot be resident with
+        # these kernels' register use (100-110 per thread), so the sweep ends
+        # at 256.
+        dims = DIMS
+        v = synth.volume(dims)
+        lat = su3s.Lattice(dims)
+        ha, hb = synth.su3(SEED, 0, v), synth.su3(SEED, 1, v)
+        for prec, pname, pipes, bsite in ((F64, "f64", ((su3s.PIPE_TMA, "tma"), (su3s.PIPE_PLAIN, "plain")), B_MM),
+                                          (su3s.F32, "f32", ((su3s.PIPE_PLAIN, "plain"),), 216)):
+            a = fld(lat, MAT, 1, prec, ha)
+            b = fld(lat, MAT, 1, prec, hb)
+            z = a.like()
+            for pipe, pipename in pipes:
+                su3s.set_pipeline(pipe)
+                for threads in (32, 64, 128, 256):
+                    for bps in (1, 2, 4, 8, 16, 0):
+                        su3s.set_launch(z, a * b, threads, bps)
+                        ms = _time_ms(torch, stream, lambda: su3s.evaluate(z, a * b, 0, stream))
+                        out.append({"study": "block shape z=a*b", "lattice": list(dims),
+                                    "storage": pname, "pipeline": pipename, "threads": threads,
+                                    "warps_per_cta": threads // 32,
+                                    "ctas_per_sm": bps if bps else "max",
+                                    "ms": round(ms, 5), "GB_s": round(bsite * v / ms / 1e6, 1)})
+            su3s.set_pipeline(su3s.PIPE_AUTO)
+            del a, b, z
             torch.cuda.empty_cache()
 
     if "batch" in which:
@@ -857,7 +904,7 @@ def main():
     ap.add_argument("--dims", default="48,48,48,48", help="lattice extents (default 48^4)")
     ap.add_argument("--study", default="",
                     help="comma list of studies to run instead of the step: volume, fused, "
-                         "precision, batch, layout, stencil, interp (one JSON line each)")
+                         "precision, batch, layout, blocks, stencil, interp (one JSON line each)")
     ap.add_argument("--math", default="df32", choices=["fx", "df32", "f64"],
                     help="arithmetic of the FP64-storage rows in the step (the others are "
                          "timed beside it)")

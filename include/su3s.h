@@ -472,6 +472,27 @@ int su3s_cshift(su3s_field* dst, const su3s_field* src, int dim, int shift, void
  * overlapping U or v: EINVAL.  Pad sites are not touched. */
 int su3s_hop(su3s_field* dst, const su3s_field* U, const su3s_field* v, int math, void* stream);
 
+/* The Wilson Dslash hopping term with its spin structure (the operator the
+ * paper names for its port to GPUs, Sec. 6):
+ *   dst(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x + mu)
+ *                   + (1 + gamma_mu) U_mu(x - mu)^dagger psi(x - mu) ]
+ * with Euclidean gamma matrices in the chiral basis:
+ *   gamma_mu = [[0, s_mu], [s_mu^dagger, 0]] in 2x2 spin blocks,
+ *   s_x = [[0, i], [i, 0]], s_y = [[0, -1], [1, 0]], s_z = [[i, 0], [0, -i]],
+ *   s_t = 1 (so gamma_5 = gamma_x gamma_y gamma_z gamma_t = diag(1, 1, -1, -1)).
+ * A spinor field is a colour-vector field with nmu = 4 objects per site,
+ * object s being spin component s (canonical host layout
+ * double[V][4][3][2]: site, spin, colour, re/im).  psi and dst: such fields;
+ * U: a matrix field with 4 links per site (ETYPE otherwise); all FP64
+ * storage (EUNSUPPORTED otherwise), one lattice (ESHAPE otherwise), any
+ * layouts.  Each term projects psi to a two-component half spinor, multiplies
+ * it by the link and rebuilds the four spin components; the products are
+ * accumulated in the arithmetic `math` (as for su3s_eval_math, with its range
+ * guard; EINVAL for another value).  dst overlapping U or psi: EINVAL.  Pad
+ * sites are not touched. */
+int su3s_dslash(su3s_field* dst, const su3s_field* U, const su3s_field* psi, int math,
+                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,7 @@ def load(build_if_missing=False):
         "su3s_reunitarize": ([P, P, P], I),
         "su3s_cshift": ([P, P, I, I, P], I),
         "su3s_hop": ([P, P, P, I, P], I),
+        "su3s_dslash": ([P, P, P, I, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -513,6 +514,15 @@ def hop(dst, links, v, math=MATH_DEFAULT, stream=None):
     """dst(x) = sum_mu U_mu(x) v(x+mu) + U_mu(x-mu)^dagger v(x-mu), the colour
     part of the Dslash hopping term; `links` holds the 4 links of every site."""
     _check(_lib.su3s_hop(dst._h, links._h, v._h, math, _stream(stream)))
+    return dst
+
+
+def dslash(dst, links, psi, math=MATH_DEFAULT, stream=None):
+    """dst(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu)
+    U_mu(x-mu)^dagger psi(x-mu), the Wilson hopping term with spin (chiral
+    gamma basis); psi and dst are colour-vector fields with 4 spin components
+    per site (nmu = 4), `links` holds the 4 links of every site."""
+    _check(_lib.su3s_dslash(dst._h, links._h, psi._h, math, _stream(stream)))
     return dst
 
 

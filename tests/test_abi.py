@@ -298,6 +298,19 @@ def test_neighbour_operation_validation(L):
     assert L.su3s_hop(f32, u4, m2, 0, None) == 6                  # FP64 only
     assert L.su3s_hop(mo, u4, m2, 0, None) == 3                   # lattice
     assert L.su3s_hop(v2, u4, v1, 9, None) == 1                   # arithmetic
+    # the Wilson hopping term: spinors are vector fields with 4 spin components
+    s1 = _wrap(L, lat, su3s.VECTOR, 4, su3s.F64, FAKE + 7 * gap)
+    s2 = _wrap(L, lat, su3s.VECTOR, 4, su3s.F64, FAKE + 8 * gap)
+    s32 = _wrap(L, lat, su3s.VECTOR, 4, su3s.F32, FAKE + 9 * gap)
+    so = _wrap(L, other, su3s.VECTOR, 4, su3s.F64, FAKE + 10 * gap)
+    assert L.su3s_dslash(s2, m2, s1, 0, None) == 2                # links need 4 per site
+    assert L.su3s_dslash(s2, u4, v1, 0, None) == 2                # psi: 4 spin components
+    assert L.su3s_dslash(v2, u4, s1, 0, None) == 2                # dst: 4 spin components
+    assert L.su3s_dslash(s1, u4, s1, 0, None) == 1                # overlap
+    assert L.su3s_dslash(s32, u4, s1, 0, None) == 6               # FP64 only
+    assert L.su3s_dslash(so, u4, s1, 0, None) == 3                # lattice
+    assert L.su3s_dslash(s2, u4, s1, 9, None) == 1                # arithmetic
+    assert L.su3s_dslash(None, u4, s1, 0, None) == 1              # null
 
 
 def test_batch_rejects_items_that_touch_each_other(L):
