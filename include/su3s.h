@@ -410,17 +410,33 @@ int su3s_batch_destroy(su3s_batch* b);
  * equal the number of unique leaves.  For z = a*b this is dA = G B^dagger,
  * dB = A^dagger G; sums, scalings and adjoints follow the chain rule.
  * One pass: every leaf and grad_out is read once, every gradient written
- * once.  FP64 storage only; catalogue trees only (EUNSUPPORTED otherwise). */
+ * once (a sum of two products of distinct leaves may instead run as two
+ * single-product passes, see su3s_tune_adjoint).  FP64 storage only;
+ * catalogue trees only (EUNSUPPORTED otherwise). */
 int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* grad_out, su3s_field* const* grad_leaves,
                       int nleaves, int math, void* stream);
 
 /* Autotune the reverse-mode kernel of `e` as su3s_tune does the forward one:
  * arguments as for su3s_eval_adjoint (grad_leaves are overwritten while
  * timing), result as for su3s_tune; later su3s_eval_adjoint calls on fields
- * of this shape use the fastest geometry. */
+ * of this shape use the fastest geometry.  For a sum or difference of two
+ * products of four distinct leaves (a*b + c*d, a*b - c*d, s0 a*b + s1 c*d) it
+ * also times the reverse mode split into two single-product launches,
+ * (a, b, grad_out -> dA, dB) then (c, d, grad_out -> dC, dD), which read
+ * grad_out twice but hold the operands of one product at a time, and keeps
+ * the faster form for later calls (a split choice is reported as
+ * *variant = 10 + the halves' data-movement variant).  Untuned calls of such
+ * trees run split. */
 int su3s_tune_adjoint(const su3s_expr* e, const su3s_field* grad_out, su3s_field* const* grad_leaves,
                       int nleaves, int math, void* stream, int* threads, int* blocks_per_sm,
                       int* variant, float* best_ms);
+
+/* How su3s_eval_adjoint runs the reverse mode of a sum or difference of two
+ * products of distinct leaves (process-wide; results agree within the
+ * arithmetic's error either way): -1 the tuned choice, split when untuned
+ * (default); 0 always one fused pass; 1 always two single-product passes.
+ * EINVAL for other values. */
+int su3s_set_adjoint_split(int mode);
 
 /* Number of unique leaves of `e` in *n. */
 int su3s_expr_num_leaves(const su3s_expr* e, int* n);

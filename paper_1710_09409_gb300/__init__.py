@@ -109,6 +109,7 @@ def load(build_if_missing=False):
         "su3s_cshift": ([P, P, I, I, P], I),
         "su3s_hop": ([P, P, P, I, P], I),
         "su3s_dslash": ([P, P, P, I, P], I),
+        "su3s_set_adjoint_split": ([I], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -473,6 +474,12 @@ def eval_adjoint(expr, grad_out, grads, math=MATH_DEFAULT, stream=None):
     expr = _as_expr(expr)
     arr = (ctypes.c_void_p * max(1, len(grads)))(*[(g._h if g is not None else None) for g in grads])
     _check(_lib.su3s_eval_adjoint(expr._h, grad_out._h, arr, len(grads), math, _stream(stream)))
+
+
+def set_adjoint_split(mode):
+    """Reverse mode of a sum of two products: -1 tuned (split when untuned),
+    0 one fused pass, 1 two single-product passes."""
+    _check(load().su3s_set_adjoint_split(int(mode)))
 
 
 def tune_adjoint(expr, grad_out, grads, math=MATH_DEFAULT, stream=None):

@@ -8,6 +8,7 @@ template <class M>
 static void adj_set(int m) {
   using namespace cat;
   reg_adjoint<MM, M>(m);
+  reg_adjoint<ScaleMM, M>(m);  // a scaled half of a split sum of two products
   reg_adjoint<AdjMM, M>(m);
   reg_adjoint<MAdjM, M>(m);
   reg_adjoint<MV, M>(m);

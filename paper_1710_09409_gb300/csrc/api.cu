@@ -1087,6 +1087,92 @@ static int prepare_adjoint(const su3s_expr* e, const su3s_field* gout, su3s_fiel
   return SU3S_OK;
 }
 
+// Reverse mode of a sum or difference of two products of distinct leaves
+// (a*b + c*d, a*b - c*d, s0 a*b + s1 c*d) as two single-product reverse-mode
+// launches, (a, b, dL/dZ -> dA, dB) and (c, d, dL/dZ -> dC, dD).  Each launch
+// reads dL/dZ, so the split moves one object more per site (1,440 instead of
+// 1,296 B per site in FP64), but each kernel holds the operands of one
+// product only.  su3s_tune_adjoint times both forms and keeps the faster.
+struct SplitAdjoint {
+  GParams p[2];
+  const EvalEntry* ent[2];
+  bool tma[2];
+};
+
+static bool plan_split_adjoint(const su3s_expr* e, const su3s_field* gout,
+                               su3s_field* const* gleaves, int math, SplitAdjoint* out) {
+  Canon c;
+  if (canonicalize(e, &c) || c.leaves.size() != 4) return false;
+  double s[2];
+  if (c.sig == "add(mul(M0,M1),mul(M2,M3))") {
+    s[0] = 1.0;
+    s[1] = 1.0;
+  } else if (c.sig == "sub(mul(M0,M1),mul(M2,M3))") {
+    s[0] = 1.0;
+    s[1] = -1.0;
+  } else if (c.sig == "add(scale(s0,mul(M0,M1)),scale(s1,mul(M2,M3)))") {
+    s[0] = c.scalars[0];
+    s[1] = c.scalars[1];
+  } else {
+    return false;
+  }
+  const int m = math_for(SU3S_F64, math);
+  for (int h = 0; h < 2; ++h) {
+    Canon ch;
+    ch.kind = SU3S_MATRIX;
+    ch.leaves = {c.leaves[2 * h], c.leaves[2 * h + 1]};
+    if (s[h] == 1.0) {
+      ch.sig = "mul(M0,M1)";
+    } else {
+      ch.sig = "scale(s0,mul(M0,M1))";
+      ch.scalars = {s[h]};
+    }
+    out->ent[h] = find_adjoint(ch.sig, m);
+    if (!out->ent[h]) return false;
+    GParams& p = out->p[h];
+    memset(&p, 0, sizeof p);
+    build_params(ch, gout, 1, &p.k);
+    p.gout = gout->desc;
+    p.tm_gout = gout->tmap;
+    for (int i = 0; i < 2; ++i)
+      if (gleaves && gleaves[2 * h + i]) p.gleaf[i] = gleaves[2 * h + i]->desc;
+    out->tma[h] = tma_tree_ok(ch, gout);
+  }
+  return true;
+}
+
+// Whether the reverse mode of a tree, arithmetic and shape runs split (set by
+// su3s_tune_adjoint; absent: kSplitDefault).
+static std::mutex g_adj_mode_mu;
+static std::map<std::tuple<std::string, int, int64_t, int>, bool>& adj_mode() {
+  static std::map<std::tuple<std::string, int, int64_t, int>, bool> m;
+  return m;
+}
+static constexpr bool kSplitDefault = true;
+
+// -1: tuned choice (or kSplitDefault); 0: always fused; 1: always split
+static std::atomic<int> g_split_pref{-1};
+
+static bool use_split(const std::string& sig, int m, int64_t nvec, int nmu) {
+  const int pref = g_split_pref.load(std::memory_order_relaxed);
+  if (pref >= 0) return pref == 1;
+  std::lock_guard<std::mutex> lk(g_adj_mode_mu);
+  auto it = adj_mode().find(std::make_tuple(sig, m, nvec, nmu));
+  return it == adj_mode().end() ? kSplitDefault : it->second;
+}
+
+static cudaError_t launch_planned(const EvalEntry* ent, const GParams& p, bool tma, cudaStream_t st) {
+  Launch L;
+  plan_launch(ent, p.k.nvec, p.k.nmu, tma, &L);
+  return L.fn(&p, L.grid, L.block, st);
+}
+
+SU3S_EXPORT int su3s_set_adjoint_split(int mode) {
+  if (mode < -1 || mode > 1) return fail(SU3S_EINVAL, "split mode must be -1, 0 or 1");
+  g_split_pref.store(mode, std::memory_order_relaxed);
+  return ok();
+}
+
 SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
                                   su3s_field* const* gleaves, int nleaves, int math, void* stream) {
   GParams p;
@@ -1094,11 +1180,49 @@ SU3S_EXPORT int su3s_eval_adjoint(const su3s_expr* e, const su3s_field* gout,
   bool tma = false;
   int rc = prepare_adjoint(e, gout, gleaves, nleaves, math, &p, &ent, &tma);
   if (rc) return rc;
-  Launch L;
-  plan_launch(ent, p.k.nvec, p.k.nmu, tma, &L);
-  cudaError_t ce = L.fn(&p, L.grid, L.block, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  Canon c;
+  canonicalize(e, &c);
+  SplitAdjoint sp;
+  cudaError_t ce;
+  if (use_split(c.sig, math_for(SU3S_F64, math), p.k.nvec, p.k.nmu) &&
+      plan_split_adjoint(e, gout, gleaves, math, &sp)) {
+    ce = launch_planned(sp.ent[0], sp.p[0], sp.tma[0], st);
+    if (ce == cudaSuccess) ce = launch_planned(sp.ent[1], sp.p[1], sp.tma[1], st);
+  } else {
+    ce = launch_planned(ent, p, tma, st);
+  }
   if (ce != cudaSuccess) return cuda_fail(ce, "adjoint kernel launch");
   return ok();
+}
+
+// Best of two runs of three launches of both halves of a split reverse mode.
+static int time_split(const SplitAdjoint& sp, cudaStream_t st, float* ms_out) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(SU3S_ECUDA, "event creation failed");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(SU3S_ECUDA, "event creation failed");
+  }
+  float best = 1e30f;
+  cudaError_t ce = cudaSuccess;
+  for (int trial = 0; trial < 3 && ce == cudaSuccess; ++trial) {  // trial 0 warms up
+    ce = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {
+      ce = launch_planned(sp.ent[0], sp.p[0], sp.tma[0], st);
+      if (ce == cudaSuccess) ce = launch_planned(sp.ent[1], sp.p[1], sp.tma[1], st);
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+    if (ce == cudaSuccess && trial > 0 && t / 3.f < best) best = t / 3.f;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return cuda_fail(ce, "timing the split reverse mode");
+  *ms_out = best;
+  return SU3S_OK;
 }
 
 SU3S_EXPORT int su3s_tune_adjoint(const su3s_expr* e, const su3s_field* gout,
@@ -1110,6 +1234,42 @@ SU3S_EXPORT int su3s_tune_adjoint(const su3s_expr* e, const su3s_field* gout,
   bool tma = false;
   int rc = prepare_adjoint(e, gout, gleaves, nleaves, math, &p, &ent, &tma);
   if (rc) return rc;
-  return tune_entry(ent, &p, p.k.nvec, p.k.nmu, tma, (cudaStream_t)stream, threads_out, bps_out,
-                    variant_out, best_ms);
+  cudaStream_t st = (cudaStream_t)stream;
+  int th = 0, bps = 0, var = 0;
+  float ms = 0.f;
+  rc = tune_entry(ent, &p, p.k.nvec, p.k.nmu, tma, st, &th, &bps, &var, &ms);
+  if (rc) return rc;
+  Canon c;
+  canonicalize(e, &c);
+  const int m = math_for(SU3S_F64, math);
+  SplitAdjoint sp;
+  if (plan_split_adjoint(e, gout, gleaves, math, &sp)) {
+    // tune each distinct half kernel, then time the pair as it runs
+    int th2 = 0, bps2 = 0, var2 = 0;
+    float ms_half = 0.f;
+    rc = tune_entry(sp.ent[0], &sp.p[0], p.k.nvec, p.k.nmu, sp.tma[0], st, &th2, &bps2, &var2,
+                    &ms_half);
+    if (!rc && sp.ent[1] != sp.ent[0])
+      rc = tune_entry(sp.ent[1], &sp.p[1], p.k.nvec, p.k.nmu, sp.tma[1], st, nullptr, nullptr,
+                      nullptr, &ms_half);
+    float ms_split = 0.f;
+    if (!rc) rc = time_split(sp, st, &ms_split);
+    if (rc) return rc;
+    const bool split = ms_split < ms;
+    {
+      std::lock_guard<std::mutex> lk(g_adj_mode_mu);
+      adj_mode()[std::make_tuple(c.sig, m, p.k.nvec, p.k.nmu)] = split;
+    }
+    if (split) {
+      th = th2;
+      bps = bps2;
+      var = 10 + var2;
+      ms = ms_split;
+    }
+  }
+  if (threads_out) *threads_out = th;
+  if (bps_out) *bps_out = bps;
+  if (variant_out) *variant_out = var;
+  if (best_ms) *best_ms = ms;
+  return ok();
 }

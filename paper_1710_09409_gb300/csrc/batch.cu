@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_batch_tma(const BItem* __restrict__ ite
       issue_tile<Tree, P_F64, false>(lane, items[Tn.item].k, nullptr, nullptr, Tn.s0, Tn.mu, buf, bar);
 #pragma unroll
     for (int k = 0; k < (NS > 0 ? NS : 1); ++k) ctx.sc[k] = M::scalar(p.sc[k], p.sch[k], p.scl[k]);
-    if (M::kGuard && guard_trips<Tree>(ctx.gmax)) {
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(ctx.gmax))) {
       eval_site_f64<Tree, P_F64>(p, T.s0 + lane, T.mu);
     } else {
       typename M::A acc[1][W];

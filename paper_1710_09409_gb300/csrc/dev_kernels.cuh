@@ -507,7 +507,9 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
     __syncwarp();
     const int64_t tn = t + wstride;
     if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, nullptr, tn << 5, mu, buf, bar);
-    if (M::kGuard && guard_trips<Tree>(ctx.gmax)) {
+    // a tile with a site out of range runs all its sites in native FP64: the
+    // decision is warp-uniform, so the hot path has no divergent branch
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(ctx.gmax))) {
       eval_site_f64<Tree, PREC>(p, (t << 5) + lane, mu);
     } else {
       typename M::A acc[1][W];
@@ -571,7 +573,7 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
     __syncwarp();
     const int64_t tn = t + wstride;
     if (tn < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, &p.tm_gout, tn << 5, mu, buf, bar);
-    if (M::kGuard && guard_trips<Tree>(max(ctx.gmax, g.gmax))) {
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(max(ctx.gmax, g.gmax)))) {
       adj_site_f64<Tree>(p, (t << 5) + lane, mu);
     } else {
       GradAcc<M, NL> ga;
@@ -786,7 +788,8 @@ __device__ __forceinline__ void lazy_range(const KParams& p, Range rg, unsigned 
     }
     c.template refill_repeated<0>();
     if (c.dead) break;
-    if (M::kGuard && guard_trips<Tree>(c.gmax)) eval_site_f64<Tree, PREC>(p, (t << 5) + c.lane, c.mu);
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(c.gmax)))
+      eval_site_f64<Tree, PREC>(p, (t << 5) + c.lane, c.mu);
     else store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
     c.parity ^= 1;
     t = tn;
@@ -795,7 +798,7 @@ __device__ __forceinline__ void lazy_range(const KParams& p, Range rg, unsigned 
 }
 
 template <class Tree, class M, int PREC>
-__global__ void __launch_bounds__(128, 4) k_eval_lazy(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, 3) k_eval_lazy(const __grid_constant__ KParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (!smem_aligned(smem, p.err)) return;
   lazy_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);
@@ -830,7 +833,8 @@ __device__ __forceinline__ void adj_lazy_range(const GParams& p, Range rg, unsig
     if (c.dead) break;
     // leaves are read as the reverse pass needs them, so the range is known
     // only now: a site out of range overwrites its gradients in native FP64
-    if (M::kGuard && guard_trips<Tree>(c.gmax)) adj_site_f64<Tree>(p, (t << 5) + c.lane, c.mu);
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(c.gmax)))
+      adj_site_f64<Tree>(p, (t << 5) + c.lane, c.mu);
     c.parity ^= 1;
     t = tn;
   }
@@ -1125,7 +1129,8 @@ __device__ __forceinline__ void ring_range(const KParams& p, Range rg, unsigned 
       for (int r = 0; r < W; ++r) acc[0][r] = M::to_acc(val[r]);
     }
     if (c.dead) break;
-    if (M::kGuard && guard_trips<Tree>(c.gmax)) eval_site_f64<Tree, PREC>(p, (t << 5) + c.lane, c.mu);
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(c.gmax)))
+      eval_site_f64<Tree, PREC>(p, (t << 5) + c.lane, c.mu);
     else store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + c.lane, c.mu, acc);
     t = tn;
   }
@@ -1166,7 +1171,8 @@ __device__ __forceinline__ void adj_ring_range(const GParams& p, Range rg, unsig
     store_repeated<Tree, 0, M>(ga, sink);
     if (c.dead) break;
     // as in the per-leaf variant: the range is known after the reverse pass
-    if (M::kGuard && guard_trips<Tree>(c.gmax)) adj_site_f64<Tree>(p, (t << 5) + c.lane, c.mu);
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(c.gmax)))
+      adj_site_f64<Tree>(p, (t << 5) + c.lane, c.mu);
     t = tn;
   }
   if (c.dead) c.drain();
@@ -1435,6 +1441,7 @@ void reg_adjoint(int math) {
 // ------------------------------------------------------------ catalogue
 namespace cat {
 using MM = Mul<LM<0>, LM<1>>;
+using ScaleMM = Scale<0, Mul<LM<0>, LM<1>>>;
 using AdjMM = Mul<Adj<LM<0>>, LM<1>>;
 using MAdjM = Mul<LM<0>, Adj<LM<1>>>;
 using AdjMAdjM = Mul<Adj<LM<0>>, Adj<LM<1>>>;

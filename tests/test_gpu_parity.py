@@ -490,6 +490,46 @@ def test_adjoint_kernels(su3s, name, tree, math):
         assert np.abs(g.download() - ref[n]).max() < TOL * wscale, n
 
 
+E1SUB = ("sub", ("mul", ("leaf", "a"), ("leaf", "b")), ("mul", ("leaf", "c"), ("leaf", "d")))
+E1LIN = ("add", ("scale", 0.75, ("mul", ("leaf", "a"), ("leaf", "b"))),
+         ("scale", -1.5, ("mul", ("leaf", "c"), ("leaf", "d"))))
+
+
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
+@pytest.mark.parametrize("name,tree", [("E1", E1), ("E1Sub", E1SUB), ("E1Lin", E1LIN)],
+                         ids=["E1", "E1Sub", "E1Lin"])
+@pytest.mark.parametrize("pipeline", [-1, 0, 2], ids=["auto", "plain", "leaf"])
+def test_adjoint_split_and_fused_agree(su3s, name, tree, math, pipeline):
+    # a sum of two products of distinct leaves: one fused pass and two
+    # single-product passes give the oracle's gradients (E1: bit for bit the
+    # same, each half repeats the fused kernel's operations for its product)
+    dims = (6, 5, 7, 3)
+    lat = su3s.Lattice(dims)
+    names = oracle.leaf_names(tree)
+    f = lattice_fields(dims, SEED + 5, names=tuple(names) + ("w",))
+    F = {n: upload(su3s, lat, f[n]) for n in names}
+    G = upload(su3s, lat, f["w"])
+    ref = oracle.eval_adjoint(tree, {n: f[n] for n in names}, f["w"])
+    wscale = np.abs(f["w"]).max() * 3 * 1.5
+    got = {}
+    su3s.set_pipeline(pipeline)
+    try:
+        for mode in (0, 1):
+            su3s.set_adjoint_split(mode)
+            grads = [F[n].like() for n in names]
+            su3s.eval_adjoint(tree_expr(tree, F), G, grads, math)
+            got[mode] = [g.download() for g in grads]
+    finally:
+        su3s.set_adjoint_split(-1)
+        su3s.set_pipeline(-1)
+    for mode in (0, 1):
+        for n, g in zip(names, got[mode]):
+            assert np.abs(g - ref[n]).max() < TOL * wscale, (mode, n)
+    if name == "E1":
+        for a, b in zip(got[0], got[1]):
+            assert a.tobytes() == b.tobytes()
+
+
 @pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_adjoint_matrix_vector(su3s, math):
     dims = (6, 5, 7, 3)
