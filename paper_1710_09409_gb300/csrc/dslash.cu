@@ -30,14 +30,6 @@
 
 namespace su3s {
 
-// Phase of row k of s_mu as a compile-time code: 0 = 1, 1 = i, 2 = -1, 3 = -i,
-// and the column of its entry.
-template <int MU, int K>
-struct SigmaEntry {
-  static constexpr int col = (MU <= 1) ? 1 - K : K;
-  static constexpr int phase = MU == 0 ? 1 : MU == 1 ? (K == 0 ? 2 : 0) : MU == 2 ? (K == 0 ? 1 : 3) : 0;
-};
-
 // acc (+)= P * x for a complex x given as (re, im) values, P = i^code.
 template <class M, bool FIRST, int CODE>
 __device__ __forceinline__ void add_phased(typename M::A& are, typename M::A& aim,
@@ -76,69 +68,39 @@ __device__ __forceinline__ void combine_phased(typename M::A& are, typename M::A
   }
 }
 
-// Component k of the half spinor, h_k = u_k + SG s_mu(k, col) l_col, from the
-// neighbour's four spin components sp.
-template <class M, int MU, int SG, int K>
-__device__ __forceinline__ void half_spinor(typename M::R* h, const typename M::R (*sp)[6]) {
-  using E = SigmaEntry<MU, K>;
-  constexpr int ph = (E::phase + (SG > 0 ? 0 : 2)) & 3;
+// h = u + P l for one spin component pair, P = i^ph (ph uniform across the
+// warp: one of four compiled forms).
+template <class M>
+__device__ __forceinline__ void half_spinor(typename M::R* h, const typename M::R* u,
+                                            const typename M::R* l, int ph) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     typename M::A re, im;
-    M::template add<true, 1>(re, sp[K][2 * c]);
-    M::template add<true, 1>(im, sp[K][2 * c + 1]);
-    add_phased<M, false, ph>(re, im, sp[2 + E::col][2 * c], sp[2 + E::col][2 * c + 1]);
+    M::template add<true, 1>(re, u[2 * c]);
+    M::template add<true, 1>(im, u[2 * c + 1]);
+    switch (ph) {
+      case 0: add_phased<M, false, 0>(re, im, l[2 * c], l[2 * c + 1]); break;
+      case 1: add_phased<M, false, 1>(re, im, l[2 * c], l[2 * c + 1]); break;
+      case 2: add_phased<M, false, 2>(re, im, l[2 * c], l[2 * c + 1]); break;
+      default: add_phased<M, false, 3>(re, im, l[2 * c], l[2 * c + 1]); break;
+    }
     h[2 * c] = M::finish(re);
     h[2 * c + 1] = M::finish(im);
   }
 }
 
-// chi = U h_k (U^dagger for the backward term) into upper spin k, and
-// SG conj(s_mu(k, col)) chi into lower spin col.
-template <class M, int MU, int SG, int K>
-__device__ __forceinline__ void rebuild(typename M::A (*out)[6], const typename M::R* u,
-                                        const typename M::R* h) {
-  using E = SigmaEntry<MU, K>;
-  constexpr int ph = (((4 - E::phase) & 3) + (SG > 0 ? 0 : 2)) & 3;
-  typename M::A chi[6];
-  mv_acc<M, true, 1, (SG > 0)>(chi, u, h);
+// out += P chi for a colour vector of accumulators, P = i^ph (uniform).
+template <class M>
+__device__ __forceinline__ void add_rebuilt(typename M::A* out, const typename M::A* chi, int ph) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    combine_phased<M, 0>(out[K][2 * c], out[K][2 * c + 1], chi[2 * c], chi[2 * c + 1]);
-    combine_phased<M, ph>(out[2 + E::col][2 * c], out[2 + E::col][2 * c + 1], chi[2 * c],
-                          chi[2 * c + 1]);
+    switch (ph) {
+      case 0: combine_phased<M, 0>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
+      case 1: combine_phased<M, 1>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
+      case 2: combine_phased<M, 2>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
+      default: combine_phased<M, 3>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
+    }
   }
-}
-
-// One term: direction MU, forward (SG = -1: U_mu(x), psi(x+mu)) or backward
-// (SG = +1: U_mu(x-mu)^dagger, psi(x-mu)); out[spin][6] accumulators.
-template <class M, int MU, int SG>
-__device__ __forceinline__ void dslash_term(typename M::A (*out)[6], const FieldDesc& U,
-                                            const FieldDesc& psi, const LatGeo& g, int64_t s,
-                                            uint32_t& gm) {
-  constexpr bool BWD = SG > 0;
-  const int64_t n = shift_site(g, s, MU, BWD ? -1 : 1);
-  typename M::R h[2][6];
-  {
-    typename M::R sp[4][6];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) load_nc<M, 6>(psi, n, k, sp[k], gm);
-    half_spinor<M, MU, SG, 0>(h[0], sp);
-    half_spinor<M, MU, SG, 1>(h[1], sp);
-  }
-  if constexpr (M::kScaled) {
-    // fixed point: the half spinor's components share one exponent
-    typename M::A a[12];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-      for (int r = 0; r < 6; ++r) a[6 * k + r] = M::to_acc(h[k][r]);
-    M::template finish_obj<12>(&h[0][0], a);
-  }
-  typename M::R u[18];
-  load_nc<M, 18>(U, BWD ? n : s, MU, u, gm);
-  rebuild<M, MU, SG, 0>(out, u, h[0]);
-  rebuild<M, MU, SG, 1>(out, u, h[1]);
 }
 
 template <class M>
@@ -146,7 +108,12 @@ __device__ __noinline__ void dslash_site_f64(const FieldDesc& dst, const FieldDe
                                              const FieldDesc& psi, const LatGeo& g, int64_t s);
 
 // The eight terms at site s, then the store (or, for a site whose inputs are
-// outside the FP64-accurate arithmetics' range, native FP64 instead).
+// outside the FP64-accurate arithmetics' range, native FP64 instead).  The
+// terms run in a rolled loop: unrolled, the eight bodies (~10,000 instructions
+// per site in the pair arithmetic) overflowed the instruction cache and
+// instruction fetch was the leading stall.  Direction and sense are uniform
+// across the warp, so the phase and column choices are uniform branches; the
+// backward link's adjoint is taken in its load.
 template <class M>
 __device__ __forceinline__ void dslash_site(const FieldDesc& dst, const FieldDesc& U,
                                             const FieldDesc& psi, const LatGeo& g, int64_t s) {
@@ -156,14 +123,57 @@ __device__ __forceinline__ void dslash_site(const FieldDesc& dst, const FieldDes
 #pragma unroll
     for (int r = 0; r < 6; ++r) out[k][r] = M::zero();
   uint32_t gm = 0;
-  dslash_term<M, 0, -1>(out, U, psi, g, s, gm);
-  dslash_term<M, 0, 1>(out, U, psi, g, s, gm);
-  dslash_term<M, 1, -1>(out, U, psi, g, s, gm);
-  dslash_term<M, 1, 1>(out, U, psi, g, s, gm);
-  dslash_term<M, 2, -1>(out, U, psi, g, s, gm);
-  dslash_term<M, 2, 1>(out, U, psi, g, s, gm);
-  dslash_term<M, 3, -1>(out, U, psi, g, s, gm);
-  dslash_term<M, 3, 1>(out, U, psi, g, s, gm);
+#pragma unroll 1
+  for (int t = 0; t < 8; ++t) {
+    const int mu = t >> 1;
+    const bool bwd = (t & 1) != 0;          // sense: SG = +1 backward, -1 forward
+    const int64_t n = shift_site_rt(g, s, mu, bwd ? -1 : 1);
+    // s_mu: row k has its entry in column k ^ sw with phase code ph_k
+    const bool sw = mu < 2;
+    const int ph0 = mu == 0 ? 1 : mu == 1 ? 2 : mu == 2 ? 1 : 0;
+    const int ph1 = mu == 0 ? 1 : mu == 1 ? 0 : mu == 2 ? 3 : 0;
+    const int sg = bwd ? 0 : 2;             // phase code of SG
+    typename M::R h[2][6];
+    {
+      typename M::R sp[4][6];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) load_nc<M, 6>(psi, n, k, sp[k], gm);
+      if (sw) {
+        half_spinor<M>(h[0], sp[0], sp[3], (ph0 + sg) & 3);
+        half_spinor<M>(h[1], sp[1], sp[2], (ph1 + sg) & 3);
+      } else {
+        half_spinor<M>(h[0], sp[0], sp[2], (ph0 + sg) & 3);
+        half_spinor<M>(h[1], sp[1], sp[3], (ph1 + sg) & 3);
+      }
+    }
+    if constexpr (M::kScaled) {
+      // fixed point: the half spinor's components share one exponent
+      typename M::A a[12];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int r = 0; r < 6; ++r) a[6 * k + r] = M::to_acc(h[k][r]);
+      M::template finish_obj<12>(&h[0][0], a);
+    }
+    typename M::R u[18];
+    load_link<M>(U, bwd ? n : s, mu, bwd, u, gm);
+    // upper spin k += U h_k; lower spin (k ^ sw) += SG conj(P_k) U h_k
+    const int q0 = (((4 - ph0) & 3) + sg) & 3, q1 = (((4 - ph1) & 3) + sg) & 3;
+    {
+      typename M::A chi[6];
+      mv_acc<M, true, 1, false>(chi, u, h[0]);
+      add_rebuilt<M>(out[0], chi, 0);
+      if (sw) add_rebuilt<M>(out[3], chi, q0);
+      else add_rebuilt<M>(out[2], chi, q0);
+    }
+    {
+      typename M::A chi[6];
+      mv_acc<M, true, 1, false>(chi, u, h[1]);
+      add_rebuilt<M>(out[1], chi, 0);
+      if (sw) add_rebuilt<M>(out[2], chi, q1);
+      else add_rebuilt<M>(out[3], chi, q1);
+    }
+  }
   if constexpr (M::kGuard) {
     if (gm >= guard_hi(2)) {
       dslash_site_f64<MathF64>(dst, U, psi, g, s);

@@ -79,3 +79,71 @@ def test_fp64_arithmetic_errors(su3s, dims, trees):
             line["max_abs_err_" + mname] = err
             assert err <= bound, (name, mname, err)
         print(json.dumps(line))
+
+
+def _rows(t, shape):
+    return t.reshape((-1,) + shape).numpy()
+
+
+def test_bench_step_errors_at_48(gpu_lib):
+    """Every output of every FP64-storage row of the benchmark step at its size
+    (48^4, 5,308,416 sites; the 64 batch lattices in full), tuned and run as
+    the benchmark runs them, against the oracle: the maximum absolute error per
+    row in the default (pair) arithmetic, within 1e-13 (Gaussian operands: the
+    bound scaled by their size, as in the parity tests)."""
+    import torch
+
+    import bench
+    from helpers import cplx
+    su3s = gpu_lib
+    want = lambda n: n.startswith(("A2", "A3", "A4", "A5", "A7 z=a*b f64", "A8", "A9"))
+    rows, keep = bench.build_rows(su3s, synth, torch, True, want=want)
+    stream = torch.cuda.Stream()
+    for r in rows:
+        if r.tune is not None:
+            r.tune(stream)
+    for r in rows:
+        r.run(stream)
+    stream.synchronize()
+    assert su3s.device_error() == 0
+    trees = {"A5 z=a*b+c*d": E1, "A5 z=a*b*c+0.5*d": E2, "A5 z=adj(a)*b-b*adj(a)": E3}
+    line = {"study": "fp64 error vs oracle, benchmark step", "lattice": [48, 48, 48, 48],
+            "arithmetic": "df32"}
+    for r in rows:
+        ins = [h for _, h in r.inputs]
+        outs = [f for f, _ in r.outputs]
+        name = r.name
+        if name in ("A2 z=a*b", "A4 z_mu=a_mu*b_mu"):
+            err, n = np.abs(outs[0].download() - oracle.mm(_rows(ins[0], (3, 3, 2)),
+                                                            _rows(ins[1], (3, 3, 2)))).max(), 1.0
+        elif name == "A3 z=a*v":
+            X = _rows(ins[1], (3, 2))
+            n = max(1.0, np.abs(cplx(X)).sum(axis=1).max())
+            err = np.abs(outs[0].download() - oracle.mv(_rows(ins[0], (3, 3, 2)), X)).max()
+        elif name in trees:
+            leaves = {k: _rows(h, (3, 3, 2)) for k, h in zip("abcd", ins)}
+            err, n = np.abs(outs[0].download() - oracle.eval_tree(trees[name], leaves)).max(), 1.0
+        elif name == "A7 z=a*b f64_c12":
+            A, B = (_rows(h, (3, 3, 2)) for h in ins)
+            ref = oracle.mm(oracle.c12_expand(A[:, :2].copy()), oracle.c12_expand(B[:, :2].copy()))
+            got = outs[0].download()
+            err, n = max(np.abs(got[:, :2] - ref[:, :2]).max(),
+                         np.abs(got - oracle.c12_expand(ref[:, :2].copy())).max()), 1.0
+        elif name.startswith("A8"):
+            err, n = 0.0, 1.0
+            for i, z in enumerate(outs):
+                leaves = {k: _rows(h, (3, 3, 2)) for k, h in zip("abcd", ins[4 * i:4 * i + 4])}
+                err = max(err, np.abs(z.download() - oracle.eval_tree(E1, leaves)).max())
+        elif name.startswith("A9"):
+            tree = MM if name == "A9 adjoint of z=a*b" else E1
+            names = "ab" if tree is MM else "abcd"
+            leaves = {k: _rows(h, (3, 3, 2)) for k, h in zip(names, ins)}
+            W = _rows(ins[len(names)], (3, 3, 2))
+            ref = oracle.eval_adjoint(tree, leaves, W)
+            n = np.abs(W).max() * 3
+            err = max(np.abs(g.download() - ref[k]).max() for k, g in zip(names, outs))
+        else:
+            continue
+        line[name] = {"max_abs_err": float(err), "bound": 1e-13 * n}
+        assert err <= 1e-13 * n, (name, err)
+    print(json.dumps(line))
