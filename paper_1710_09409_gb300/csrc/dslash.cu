@@ -25,81 +25,57 @@
 // accumulate; the first term's accumulation is a copy).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "dev_stencil.cuh"
 #include "internal.h"
 
 namespace su3s {
 
-// acc (+)= P * x for a complex x given as (re, im) values, P = i^code.
-template <class M, bool FIRST, int CODE>
-__device__ __forceinline__ void add_phased(typename M::A& are, typename M::A& aim,
-                                           const typename M::R& xr, const typename M::R& xi) {
-  if constexpr (CODE == 0) {
-    M::template add<FIRST, 1>(are, xr);
-    M::template add<FIRST, 1>(aim, xi);
-  } else if constexpr (CODE == 1) {  // i (xr + i xi) = -xi + i xr
-    M::template add<FIRST, -1>(are, xi);
-    M::template add<FIRST, 1>(aim, xr);
-  } else if constexpr (CODE == 2) {
-    M::template add<FIRST, -1>(are, xr);
-    M::template add<FIRST, -1>(aim, xi);
-  } else {  // -i (xr + i xi) = xi - i xr
-    M::template add<FIRST, 1>(are, xi);
-    M::template add<FIRST, -1>(aim, xr);
-  }
+// Multiplication by a phase P = i^ph, ph uniform across the warp, without
+// branches: P (xr + i xi) = (sr a, si b) with (a, b) = (xr, xi) or (xi, xr)
+// (odd ph), sr = -1 for ph = 1, 2 and si = -1 for ph = 2, 3.  Negation is exact
+// in every arithmetic, so the result is the phase times the value exactly.
+struct Phase {
+  bool swap, neg_re, neg_im;
+  __device__ __forceinline__ explicit Phase(int ph)
+      : swap((ph & 1) != 0), neg_re(ph == 1 || ph == 2), neg_im(ph >= 2) {}
+};
+
+template <class M>
+__device__ __forceinline__ typename M::A neg_acc(const typename M::A& a) {
+  if constexpr (std::is_same<typename M::A, DAcc>::value) return DAcc{-a.S, -a.lo};
+  else if constexpr (std::is_same<typename M::A, FAcc>::value) return FAcc{-a.hh, -a.cr, a.e};
+  else return -a;
 }
 
-// acc += P * b for an accumulated complex b (two accumulators), P = i^code.
-template <class M, int CODE>
-__device__ __forceinline__ void combine_phased(typename M::A& are, typename M::A& aim,
-                                               const typename M::A& br, const typename M::A& bi) {
-  if constexpr (CODE == 0) {
-    M::template combine<1>(are, br);
-    M::template combine<1>(aim, bi);
-  } else if constexpr (CODE == 1) {
-    M::template combine<-1>(are, bi);
-    M::template combine<1>(aim, br);
-  } else if constexpr (CODE == 2) {
-    M::template combine<-1>(are, br);
-    M::template combine<-1>(aim, bi);
-  } else {
-    M::template combine<1>(are, bi);
-    M::template combine<-1>(aim, br);
-  }
-}
-
-// h = u + P l for one spin component pair, P = i^ph (ph uniform across the
-// warp: one of four compiled forms).
+// h = u + P l for one spin component pair (colour vectors of reals).
 template <class M>
 __device__ __forceinline__ void half_spinor(typename M::R* h, const typename M::R* u,
-                                            const typename M::R* l, int ph) {
+                                            const typename M::R* l, Phase P) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
+    const typename M::R a = P.swap ? l[2 * c + 1] : l[2 * c];
+    const typename M::R b = P.swap ? l[2 * c] : l[2 * c + 1];
     typename M::A re, im;
     M::template add<true, 1>(re, u[2 * c]);
     M::template add<true, 1>(im, u[2 * c + 1]);
-    switch (ph) {
-      case 0: add_phased<M, false, 0>(re, im, l[2 * c], l[2 * c + 1]); break;
-      case 1: add_phased<M, false, 1>(re, im, l[2 * c], l[2 * c + 1]); break;
-      case 2: add_phased<M, false, 2>(re, im, l[2 * c], l[2 * c + 1]); break;
-      default: add_phased<M, false, 3>(re, im, l[2 * c], l[2 * c + 1]); break;
-    }
+    M::template add<false, 1>(re, P.neg_re ? M::neg(a) : a);
+    M::template add<false, 1>(im, P.neg_im ? M::neg(b) : b);
     h[2 * c] = M::finish(re);
     h[2 * c + 1] = M::finish(im);
   }
 }
 
-// out += P chi for a colour vector of accumulators, P = i^ph (uniform).
+// out += P chi for a colour vector of accumulators.
 template <class M>
-__device__ __forceinline__ void add_rebuilt(typename M::A* out, const typename M::A* chi, int ph) {
+__device__ __forceinline__ void add_rebuilt(typename M::A* out, const typename M::A* chi, Phase P) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    switch (ph) {
-      case 0: combine_phased<M, 0>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
-      case 1: combine_phased<M, 1>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
-      case 2: combine_phased<M, 2>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
-      default: combine_phased<M, 3>(out[2 * c], out[2 * c + 1], chi[2 * c], chi[2 * c + 1]); break;
-    }
+    const typename M::A a = P.swap ? chi[2 * c + 1] : chi[2 * c];
+    const typename M::A b = P.swap ? chi[2 * c] : chi[2 * c + 1];
+    M::template combine<1>(out[2 * c], P.neg_re ? neg_acc<M>(a) : a);
+    M::template combine<1>(out[2 * c + 1], P.neg_im ? neg_acc<M>(b) : b);
   }
 }
 
@@ -139,11 +115,11 @@ __device__ __forceinline__ void dslash_site(const FieldDesc& dst, const FieldDes
 #pragma unroll
       for (int k = 0; k < 4; ++k) load_nc<M, 6>(psi, n, k, sp[k], gm);
       if (sw) {
-        half_spinor<M>(h[0], sp[0], sp[3], (ph0 + sg) & 3);
-        half_spinor<M>(h[1], sp[1], sp[2], (ph1 + sg) & 3);
+        half_spinor<M>(h[0], sp[0], sp[3], Phase((ph0 + sg) & 3));
+        half_spinor<M>(h[1], sp[1], sp[2], Phase((ph1 + sg) & 3));
       } else {
-        half_spinor<M>(h[0], sp[0], sp[2], (ph0 + sg) & 3);
-        half_spinor<M>(h[1], sp[1], sp[3], (ph1 + sg) & 3);
+        half_spinor<M>(h[0], sp[0], sp[2], Phase((ph0 + sg) & 3));
+        half_spinor<M>(h[1], sp[1], sp[3], Phase((ph1 + sg) & 3));
       }
     }
     if constexpr (M::kScaled) {
@@ -158,18 +134,18 @@ __device__ __forceinline__ void dslash_site(const FieldDesc& dst, const FieldDes
     typename M::R u[18];
     load_link<M>(U, bwd ? n : s, mu, bwd, u, gm);
     // upper spin k += U h_k; lower spin (k ^ sw) += SG conj(P_k) U h_k
-    const int q0 = (((4 - ph0) & 3) + sg) & 3, q1 = (((4 - ph1) & 3) + sg) & 3;
+    const Phase q0((((4 - ph0) & 3) + sg) & 3), q1((((4 - ph1) & 3) + sg) & 3), one(0);
     {
       typename M::A chi[6];
       mv_acc<M, true, 1, false>(chi, u, h[0]);
-      add_rebuilt<M>(out[0], chi, 0);
+      add_rebuilt<M>(out[0], chi, one);
       if (sw) add_rebuilt<M>(out[3], chi, q0);
       else add_rebuilt<M>(out[2], chi, q0);
     }
     {
       typename M::A chi[6];
       mv_acc<M, true, 1, false>(chi, u, h[1]);
-      add_rebuilt<M>(out[1], chi, 0);
+      add_rebuilt<M>(out[1], chi, one);
       if (sw) add_rebuilt<M>(out[2], chi, q1);
       else add_rebuilt<M>(out[3], chi, q1);
     }
@@ -193,26 +169,179 @@ __device__ __noinline__ void dslash_site_f64(const FieldDesc& dst, const FieldDe
   dslash_site<M>(dst, U, psi, g, s);
 }
 
+// ------------------------------------------------ staged (asynchronous) loads
+// Each thread stages the operands of its next term (the neighbour spinor's 12
+// complex components and the link's 9) in its own slots of shared memory with
+// asynchronous copies (cp.async) while it computes the current term, so the
+// loads' latency is hidden behind a term's arithmetic without holding the
+// next operands in registers.  Slots are [element][thread], 16 bytes each.
+constexpr int kDslashElems = 21;
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Issue the copies of term t (direction t >> 1, backward if t is odd) of site s.
+__device__ __forceinline__ void stage_term(uint4* slot, int nt, const FieldDesc& U,
+                                           const FieldDesc& psi, const LatGeo& g, int64_t s, int t) {
+  const int mu = t >> 1;
+  const bool bwd = (t & 1) != 0;
+  const int64_t n = shift_site_rt(g, s, mu, bwd ? -1 : 1);
+  const uint4* pp = reinterpret_cast<const uint4*>(psi.ptr);
+  const uint4* pu = reinterpret_cast<const uint4*>(U.ptr);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t b = elem_base(psi, n, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cp_async16(slot + (3 * k + c) * nt, pp + b + c * psi.s_c);
+  }
+  const int64_t bu = elem_base(U, bwd ? n : s, mu);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) cp_async16(slot + (12 + e) * nt, pu + bu + e * U.s_c);
+  cp_async_commit();
+}
+
+template <class M, int W>
+__device__ __forceinline__ void read_staged(const uint4* slot, int nt, int first, typename M::R* out,
+                                            uint32_t& gm) {
+#pragma unroll
+  for (int c = 0; c < W / 2; ++c) {
+    const uint4 v = slot[(first + c) * nt];
+    if constexpr (M::kGuard) gm = guard_max(gm, v.y, v.w);
+    out[2 * c] = M::from_bits(v.x, v.y);
+    out[2 * c + 1] = M::from_bits(v.z, v.w);
+  }
+  M::template normalize_obj<W>(out);
+}
+
+// The link of the term from its slots, its adjoint for the backward term
+// (element (i, j) read from (j, i), imaginary part negated).
+template <class M>
+__device__ __forceinline__ void read_staged_link(const uint4* slot, int nt, bool dag,
+                                                 typename M::R* out, uint32_t& gm) {
+  if (dag) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const uint4 v = slot[(12 + 3 * j + i) * nt];
+        if constexpr (M::kGuard) gm = guard_max(gm, v.y, v.w);
+        out[2 * (3 * i + j)] = M::from_bits(v.x, v.y);
+        out[2 * (3 * i + j) + 1] = M::from_bits(v.z, v.w ^ 0x80000000u);
+      }
+    M::template normalize_obj<18>(out);
+  } else {
+    read_staged<M, 18>(slot, nt, 12, out, gm);
+  }
+}
+
+// The Wilson term at the thread's sites s, s + stride, ...: each term's
+// operands were staged during the previous term (the first site's first term
+// before the loop), and the next term's copies are issued as soon as this
+// term's slots have been read into registers.
+template <class M>
+__device__ __forceinline__ void dslash_staged(const FieldDesc& dst, const FieldDesc& U,
+                                              const FieldDesc& psi, const LatGeo& g, int64_t s,
+                                              int64_t stride, uint4* slot, int nt) {
+  if (s < g.V) stage_term(slot, nt, U, psi, g, s, 0);
+  while (s < g.V) {
+    typename M::A out[4][6];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int r = 0; r < 6; ++r) out[k][r] = M::zero();
+    uint32_t gm = 0;
+#pragma unroll 1
+    for (int t = 0; t < 8; ++t) {
+      const int mu = t >> 1;
+      const bool bwd = (t & 1) != 0;
+      const bool sw = mu < 2;
+      const int ph0 = mu == 0 ? 1 : mu == 1 ? 2 : mu == 2 ? 1 : 0;
+      const int ph1 = mu == 0 ? 1 : mu == 1 ? 0 : mu == 2 ? 3 : 0;
+      const int sg = bwd ? 0 : 2;
+      cp_async_wait_all();
+      typename M::R h[2][6];
+      {
+        typename M::R sp[4][6];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) read_staged<M, 6>(slot, nt, 3 * k, sp[k], gm);
+        if (sw) {
+          half_spinor<M>(h[0], sp[0], sp[3], Phase((ph0 + sg) & 3));
+          half_spinor<M>(h[1], sp[1], sp[2], Phase((ph1 + sg) & 3));
+        } else {
+          half_spinor<M>(h[0], sp[0], sp[2], Phase((ph0 + sg) & 3));
+          half_spinor<M>(h[1], sp[1], sp[3], Phase((ph1 + sg) & 3));
+        }
+      }
+      if constexpr (M::kScaled) {
+        typename M::A a[12];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int r = 0; r < 6; ++r) a[6 * k + r] = M::to_acc(h[k][r]);
+        M::template finish_obj<12>(&h[0][0], a);
+      }
+      typename M::R u[18];
+      read_staged_link<M>(slot, nt, bwd, u, gm);
+      // this term's slots are in registers: stage the next term
+      if (t < 7) stage_term(slot, nt, U, psi, g, s, t + 1);
+      else if (s + stride < g.V) stage_term(slot, nt, U, psi, g, s + stride, 0);
+      const Phase q0((((4 - ph0) & 3) + sg) & 3), q1((((4 - ph1) & 3) + sg) & 3), one(0);
+      {
+        typename M::A chi[6];
+        mv_acc<M, true, 1, false>(chi, u, h[0]);
+        add_rebuilt<M>(out[0], chi, one);
+        if (sw) add_rebuilt<M>(out[3], chi, q0);
+        else add_rebuilt<M>(out[2], chi, q0);
+      }
+      {
+        typename M::A chi[6];
+        mv_acc<M, true, 1, false>(chi, u, h[1]);
+        add_rebuilt<M>(out[1], chi, one);
+        if (sw) add_rebuilt<M>(out[2], chi, q1);
+        else add_rebuilt<M>(out[3], chi, q1);
+      }
+    }
+    if (M::kGuard && gm >= guard_hi(2)) {
+      dslash_site_f64<MathF64>(dst, U, psi, g, s);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const typename M::A(*o)[6] = reinterpret_cast<const typename M::A(*)[6]>(out[k]);
+        store_obj<KV, P_F64, M, 1, 6>(dst, s, k, o);
+      }
+    }
+    s += stride;
+  }
+  cp_async_wait_all();
+}
+
 // One thread per site, a grid of one wave (the neighbours of the sites in
-// flight stay in the L2 cache).
+// flight stay in the L2 cache), each thread with 21 staging slots.
 template <class M>
 __global__ void __launch_bounds__(128) k_dslash(FieldDesc dst, FieldDesc U, FieldDesc psi, LatGeo g) {
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.V;
-       s += (int64_t)gridDim.x * blockDim.x)
-    dslash_site<M>(dst, U, psi, g, s);
+  extern __shared__ __align__(16) uint4 d_slots[];
+  dslash_staged<M>(dst, U, psi, g, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                   (int64_t)gridDim.x * blockDim.x, d_slots + threadIdx.x, (int)blockDim.x);
 }
 
 template <class M>
 static cudaError_t launch_dslash(const su3s_field* dest, const su3s_field* U, const su3s_field* psi,
                                  cudaStream_t st) {
   const LatGeo g = lat_geo(psi);
+  const size_t smem = (size_t)kDslashElems * 16 * 128;
+  cudaError_t e = cudaFuncSetAttribute(k_dslash<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   int per_sm = 1;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash<M>, 128, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash<M>, 128, smem);
   if (e != cudaSuccess) return e;
   int64_t nb = (int64_t)(per_sm > 0 ? per_sm : 1) * sm_count();   // one wave
   const int64_t need = (g.V + 127) / 128;
   const dim3 grid((unsigned)(nb < need ? nb : need));
-  k_dslash<M><<<grid, 128, 0, st>>>(dest->desc, U->desc, psi->desc, g);
+  k_dslash<M><<<grid, 128, smem, st>>>(dest->desc, U->desc, psi->desc, g);
   return cudaGetLastError();
 }
 
