@@ -177,13 +177,6 @@ __device__ __noinline__ void dslash_site_f64(const FieldDesc& dst, const FieldDe
 // next operands in registers.  Slots are [element][thread], 16 bytes each.
 constexpr int kDslashElems = 21;
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // Issue the copies of term t (direction t >> 1, backward if t is odd) of site s.
 __device__ __forceinline__ void stage_term(uint4* slot, int nt, const FieldDesc& U,
                                            const FieldDesc& psi, const LatGeo& g, int64_t s, int t) {
