@@ -67,30 +67,55 @@ MATH_ERR = {"fx": "7.8e-16 - 1.6e-15",
             "df32": "3.9e-14 - 6.0e-14 (SU(3) operands, every output of the 48^4 step)",
             "f64": "3.3e-16 - 6.7e-16"}
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on a
-# 32^4 lattice (1,048,576 sites; the batch row: its 64 fixed lattices), from one
-# ncu capture of the kernels as they stand (default launches); scaled to the
-# benchmark's volume in proportion to the algorithmic bytes.  (row: kernel whose
-# counters these are, bytes, algorithmic bytes of that launch).  A row missing
-# here reports traffic null.
+# The kernel each row runs (the library's default data movement, whole-tile TMA
+# staging; pair arithmetic), as ncu names it, and launches per row run.  The
+# reverse mode of a*b+c*d runs split (two launches of the single-product reverse
+# kernel) when the tuner chose that (reported variant >= 10).
+ROW_KERNEL = {
+    "A2 z=a*b": "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 0>",
+    "A3 z=a*v": "k_eval_tma<Mul<LM<0>, LV<1>>, MathDF, 0>",
+    "A4 z_mu=a_mu*b_mu": "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 0>",
+    "A5 z=a*b+c*d": "k_eval_tma<Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>, MathDF, 0>",
+    "A5 z=a*b*c+0.5*d": "k_eval_tma<Add<Mul<Mul<LM<0>, LM<1>>, LM<2>>, Scale<0, LM<3>>>, MathDF, 0>",
+    "A5 z=adj(a)*b-b*adj(a)": "k_eval_tma<Sub<Mul<Adj<LM<0>>, LM<1>>, Mul<LM<1>, Adj<LM<0>>>>, MathDF, 0>",
+    "A7 z=a*b f64_c12": "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 4>",
+    "A8 batch 64 lattices z=a*b+c*d": "k_batch_tma<MathDF, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>",
+    "A9 adjoint of z=a*b": "k_adjoint_tma<Mul<LM<0>, LM<1>>, MathDF>",
+    "A9 adjoint of z=a*b+c*d": "k_adjoint_tma<Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>, MathDFScalar>",
+}
+KERNEL_SPLIT_ADJ = "k_adjoint_tma<Mul<LM<0>, LM<1>>, MathDF>"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
+# kernel on a 32^4 lattice (1,048,576 sites; the batch row: its 64 fixed
+# lattices), from one ncu capture of the benchmark step as it stands (default
+# launches, profiles/top_kernels_32x4.md): (bytes, algorithmic bytes of that
+# launch); scaled to the benchmark's volume in proportion to the algorithmic
+# bytes.  A kernel missing here reports traffic null.
 TRAFFIC_32 = {
-    "A2 z=a*b": ("k_eval_tma<MM,MathDF,0>", 415.9 * 1e6, 452984832),
-    "A4 z_mu=a_mu*b_mu": ("k_eval_tma<MM,MathDF,0>", 1776.5 * 1e6, 1811939328),
-    "A5 z=a*b+c*d": ("k_eval_tma<E1,MathDF,0>", 731.7 * 1e6, 754974720),
-    "A5 z=a*b*c+0.5*d": ("k_eval_tma<E2,MathDF,0>", 731.2 * 1e6, 754974720),
-    "A5 z=adj(a)*b-b*adj(a)": ("k_eval_tma<E3,MathDF,0>", 415.1 * 1e6, 452984832),
-    "A8 batch 64 lattices z=a*b+c*d": ("k_batch_tma<MathDF,E1>", 4605.5 * 1e6, 4622376960),
-    "A9 adjoint of z=a*b": ("k_adjoint_tma<MM,MathDF>", 704.5 * 1e6, 754974720),
-    "A9 adjoint of z=a*b+c*d": ("k_adjoint_tma<E1,MathDFScalar>", 1304.6 * 1e6, 1358954496),
+    "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 0>": (413.0 * 1e6, 452984832),
+    "k_eval_tma<Mul<LM<0>, LV<1>>, MathDF, 0>": (228.3 * 1e6, 251658240),
+    "k_eval_tma<Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>, MathDF, 0>": (729.1 * 1e6, 754974720),
+    "k_eval_tma<Add<Mul<Mul<LM<0>, LM<1>>, LM<2>>, Scale<0, LM<3>>>, MathDF, 0>": (728.4 * 1e6, 754974720),
+    "k_eval_tma<Sub<Mul<Adj<LM<0>>, LM<1>>, Mul<LM<1>, Adj<LM<0>>>>, MathDF, 0>": (412.6 * 1e6, 452984832),
+    "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 4>": (260.5 * 1e6, 301989888),
+    "k_batch_tma<MathDF, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>": (4603.0 * 1e6, 4622376960),
+    "k_adjoint_tma<Mul<LM<0>, LM<1>>, MathDF>": (700.8 * 1e6, 754974720),
 }
 
 
-def traffic_bytes(row_name, nbytes):
-    """Measured DRAM bytes of one launch of a row's kernel, scaled to nbytes."""
-    t = TRAFFIC_32.get(row_name)
+def traffic_bytes(kernel, nbytes):
+    """Measured DRAM bytes of one launch of a kernel, scaled to nbytes."""
+    t = TRAFFIC_32.get(kernel)
     if t is None:
         return None
-    return int(round(t[1] * nbytes / t[2]))
+    return int(round(t[0] * nbytes / t[1]))
+
+
+def row_launches(r, tuned_variant):
+    """(kernel, launches, algorithmic bytes per launch) of a row as it ran."""
+    if r.name == ROW_A9B and tuned_variant is not None and tuned_variant >= 10:
+        return KERNEL_SPLIT_ADJ, 2, B_ADJ_MM * r.sites
+    return ROW_KERNEL.get(r.name, r.name), 1, r.nbytes
 
 
 def dist_env():
@@ -1047,17 +1072,33 @@ def main():
                         "GB_s": round(gbs, 1),
                         "frac_of_peak": round(gbs / peak, 4),
                         "Gsites_s": round(r.sites / (m * 1e-3) / 1e9, 3)})
-    # dominant kernel: the largest share of the step time
-    di = int(np.argmax([np.mean(ms) for ms in per_row]))
-    dm = float(np.mean(per_row[di]))
-    achieved = rows[di].nbytes / (dm * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": rows[di].name, "achieved": round(achieved, 1),
+    # dominant kernel: the kernel with the largest share of the step time,
+    # over every row that runs it (rows are grouped by the kernel they launch,
+    # as in the launch list); achieved = algorithmic bytes per launch over its
+    # average launch time
+    variant_of = {t["row"]: t.get("variant") for t in tuned}
+    groups = {}
+    for r, ms in zip(rows, per_row):
+        k, nl, lb = row_launches(r, variant_of.get(r.name))
+        g = groups.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0.0, "rows": []})
+        g["ms"] += float(np.mean(ms))
+        g["launches"] += nl
+        g["bytes"] += nl * lb
+        g["rows"].append(r.name)
+    dk = max(groups, key=lambda k: groups[k]["ms"])
+    dg = groups[dk]
+    per_launch_bytes = dg["bytes"] / dg["launches"]
+    per_launch_ms = dg["ms"] / dg["launches"]
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dk, "rows": dg["rows"], "launches_per_step": dg["launches"],
+            "share_of_step": round(dg["ms"] / ms_step, 4), "achieved": round(achieved, 1),
             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-            else "fallback 6800 GB/s", "traffic": traffic_bytes(rows[di].name, rows[di].nbytes),
-            "traffic_source": "ncu dram__bytes_read+write at 32^4, scaled by sites",
+            else "fallback 6800 GB/s",
+            "traffic": traffic_bytes(dk, per_launch_bytes),
+            "traffic_source": "ncu dram__bytes_read+write per launch at 32^4, scaled by sites",
             "nominal_peak": 7900.0, "frac_nominal": round(achieved / 7900.0, 4),
-            "algorithmic_bytes_per_launch": rows[di].nbytes}
+            "algorithmic_bytes_per_launch": int(round(per_launch_bytes))}
     a2 = row_out[0]
 
     # the other arithmetics for the FP64 rows, reported beside (not in the step)
