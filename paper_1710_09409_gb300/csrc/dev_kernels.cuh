@@ -573,9 +573,7 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
     __syncwarp();
     const int64_t tn = t + wstride;
     if (tn < ntiles) issue_tile<Tree, P_F64, true>(lane, p.k, &p.gout, &p.tm_gout, tn << 5, mu, buf, bar);
-    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(max(ctx.gmax, g.gmax)))) {
-      adj_site_f64<Tree>(p, (t << 5) + lane, mu);
-    } else {
+    {
       GradAcc<M, NL> ga;
 #pragma unroll
       for (int i = 0; i < NL; ++i)
@@ -585,6 +583,10 @@ __device__ __forceinline__ void adj_tma_range(const GParams& p, Range rg, unsign
       Rev<Tree>::template run<Tree, M>(ctx, g.leaf[0], ga, sink);
       store_repeated<Tree, 0, M>(ga, sink);
     }
+    // the gradients overlap no input, so a tile with a site out of range is
+    // rewritten in native FP64 after the pass (no branch ahead of it)
+    if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(max(ctx.gmax, g.gmax))))
+      adj_site_f64<Tree>(p, (t << 5) + lane, mu);
     t = tn;
   }
 }
