@@ -674,7 +674,7 @@ def _time_ms(torch, stream, fn, reps=20, warm=3):
     return s0.elapsed_time(s1) / reps
 
 
-def run_studies(su3s, synth, torch, stream, which):
+def run_studies(su3s, synth, torch, stream, which, study_dims=(32, 32, 32, 32)):
     """Measurements the configurations ask for beside the step, one JSON line
     each: the L^4 volume sweep (A2-A4), fused vs term-by-term trees (32^4),
     reduced-precision and two-row storage (32^4 and 16^3x32, with each format's
@@ -860,6 +860,39 @@ def run_studies(su3s, synth, torch, stream, which):
             del U, A, B
             torch.cuda.empty_cache()
 
+    if "hop" in which:
+        # the colour hopping term alone on vectors, then on matrices, on the
+        # --dims lattice in the default arithmetic (small cases for a profiler)
+        dims = study_dims
+        v = synth.volume(dims)
+        lat = su3s.Lattice(dims)
+        U = fld(lat, MAT, 4, F64, synth.su3(SEED + 6, 0, 4 * v))
+        for kind, name, bsite in ((VEC, "vector", 576 + 48 + 48), (MAT, "matrix", 576 + 144 + 144)):
+            x = (synth.gauss_vector(SEED + 6, 4, v) if kind == VEC else synth.su3(SEED + 6, 1, v))
+            X = fld(lat, kind, 1, F64, x)
+            Z = X.like()
+            ms = _time_ms(torch, stream, lambda: su3s.hop(Z, U, X, 0, stream), reps=5, warm=2)
+            out.append({"study": "hop " + name, "lattice": list(dims), "ms": round(ms, 5),
+                        "B_per_site": bsite, "GB_s": round(bsite * v / ms / 1e6, 1)})
+            del X, Z
+        del U
+        torch.cuda.empty_cache()
+
+    if "dslash" in which:
+        # the Wilson hopping term with spin alone, on the --dims lattice, in the
+        # default arithmetic (a small case for a profiler capture)
+        dims = study_dims
+        v = synth.volume(dims)
+        lat = su3s.Lattice(dims)
+        U = fld(lat, MAT, 4, F64, synth.su3(SEED + 6, 0, 4 * v))
+        P = fld(lat, su3s.VECTOR, 4, F64, synth.gauss_vector(SEED + 6, 5, 4 * v))
+        Q = P.like()
+        ms = _time_ms(torch, stream, lambda: su3s.dslash(Q, U, P, 0, stream), reps=5, warm=2)
+        out.append({"study": "wilson dslash (spin)", "lattice": list(dims), "ms": round(ms, 5),
+                    "B_per_site": 960, "GB_s": round(960 * v / ms / 1e6, 1)})
+        del U, P, Q
+        torch.cuda.empty_cache()
+
     if "blocks" in which:
         # the vector-length / block-shape study of Sec. 5 (Fig. 4 and the 2-d
         # block): z = a*b at 48^4, GB/s against threads per CTA (32-site tiles,
@@ -964,7 +997,8 @@ def main():
     ap.add_argument("--dims", default="48,48,48,48", help="lattice extents (default 48^4)")
     ap.add_argument("--study", default="",
                     help="comma list of studies to run instead of the step: volume, fused, "
-                         "precision, batch, layout, blocks, stencil, interp (one JSON line each)")
+                         "precision, batch, layout, blocks, stencil, interp, hop, dslash (one JSON "
+                         "line each; hop and dslash run on the --dims lattice)")
     ap.add_argument("--math", default="df32", choices=["fx", "df32", "f64"],
                     help="arithmetic of the FP64-storage rows in the step (the others are "
                          "timed beside it)")
@@ -1017,7 +1051,7 @@ def main():
     su3s.set_default_math(MATH_IDS[args.math])
     if args.study:
         st = torch.cuda.Stream()
-        for line in run_studies(su3s, synth, torch, st, args.study.split(",")):
+        for line in run_studies(su3s, synth, torch, st, args.study.split(","), dims):
             print(json.dumps(line))
         return 0
     su3s.set_pipeline({"auto": su3s.PIPE_AUTO, "plain": su3s.PIPE_PLAIN, "tma": su3s.PIPE_TMA,
