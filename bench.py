@@ -67,23 +67,34 @@ MATH_ERR = {"fx": "7.8e-16 - 1.6e-15",
             "df32": "3.9e-14 - 6.0e-14 (SU(3) operands, every output of the 48^4 step)",
             "f64": "3.3e-16 - 6.7e-16"}
 
-# The kernel each row runs (the library's default data movement, whole-tile TMA
-# staging; pair arithmetic), as ncu names it, and launches per row run.  The
-# reverse mode of a*b+c*d runs split (two launches of the single-product reverse
-# kernel) when the tuner chose that (reported variant >= 10).
-ROW_KERNEL = {
-    "A2 z=a*b": "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 0>",
-    "A3 z=a*v": "k_eval_tma<Mul<LM<0>, LV<1>>, MathDF, 0>",
-    "A4 z_mu=a_mu*b_mu": "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 0>",
-    "A5 z=a*b+c*d": "k_eval_tma<Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>, MathDF, 0>",
-    "A5 z=a*b*c+0.5*d": "k_eval_tma<Add<Mul<Mul<LM<0>, LM<1>>, LM<2>>, Scale<0, LM<3>>>, MathDF, 0>",
-    "A5 z=adj(a)*b-b*adj(a)": "k_eval_tma<Sub<Mul<Adj<LM<0>>, LM<1>>, Mul<LM<1>, Adj<LM<0>>>>, MathDF, 0>",
-    "A7 z=a*b f64_c12": "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 4>",
-    "A8 batch 64 lattices z=a*b+c*d": "k_batch_tma<MathDF, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>",
-    "A9 adjoint of z=a*b": "k_adjoint_tma<Mul<LM<0>, LM<1>>, MathDF>",
-    "A9 adjoint of z=a*b+c*d": "k_adjoint_tma<Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>, MathDFScalar>",
+# The tree each FP64-storage row evaluates (pair arithmetic), as the kernels'
+# template arguments name it: (tree, arithmetic type, storage, reverse mode).
+# With the data movement the row ran with (the tuner's variant, else the
+# library's default) this gives the kernel ncu names; the reverse mode of
+# a*b+c*d runs split (two launches of the single-product reverse kernel) when
+# the tuner chose that (reported variant 10 + the halves' variant).
+T_MM = "Mul<LM<0>, LM<1>>"
+T_E1 = "Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>"
+ROW_TREE = {
+    "A2 z=a*b": (T_MM, "MathDF", 0, False),
+    "A3 z=a*v": ("Mul<LM<0>, LV<1>>", "MathDF", 0, False),
+    "A4 z_mu=a_mu*b_mu": (T_MM, "MathDF", 0, False),
+    "A5 z=a*b+c*d": (T_E1, "MathDF", 0, False),
+    "A5 z=a*b*c+0.5*d": ("Add<Mul<Mul<LM<0>, LM<1>>, LM<2>>, Scale<0, LM<3>>>", "MathDF", 0, False),
+    "A5 z=adj(a)*b-b*adj(a)": ("Sub<Mul<Adj<LM<0>>, LM<1>>, Mul<LM<1>, Adj<LM<0>>>>", "MathDF", 0, False),
+    "A7 z=a*b f64_c12": (T_MM, "MathDF", 4, False),
+    "A9 adjoint of z=a*b": (T_MM, "MathDF", 0, True),
+    "A9 adjoint of z=a*b+c*d": (T_E1, "MathDFScalar", 0, True),
 }
-KERNEL_SPLIT_ADJ = "k_adjoint_tma<Mul<LM<0>, LM<1>>, MathDF>"
+ROW_KERNEL_FIXED = {
+    "A8 batch 64 lattices z=a*b+c*d": "k_batch_tma<MathDF, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>",
+}
+FWD_KERNEL = ["k_eval<{t}, {m}, {p}>", "k_eval_tma<{t}, {m}, {p}>", "k_eval_lazy<{t}, {m}, {p}>",
+              "k_eval_ring<{t}, {m}, {p}>", "k_eval_pair<{t}>"]
+ADJ_KERNEL = ["k_adjoint<{t}, {m}>", "k_adjoint_tma<{t}, {m}>", "k_adjoint_lazy<{t}, {m}>",
+              "k_adjoint_ring<{t}, {m}>", "k_adjoint_pair<{t}>"]
+# the library's default data movement of each row's kernel when untuned
+ROW_DEFAULT_VARIANT = {"A9 adjoint of z=a*b": 4, "A9 adjoint of z=a*b+c*d": 14}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel on a 32^4 lattice (1,048,576 sites; the batch row: its 64 fixed
@@ -113,9 +124,16 @@ def traffic_bytes(kernel, nbytes):
 
 def row_launches(r, tuned_variant):
     """(kernel, launches, algorithmic bytes per launch) of a row as it ran."""
-    if r.name == ROW_A9B and tuned_variant is not None and tuned_variant >= 10:
-        return KERNEL_SPLIT_ADJ, 2, B_ADJ_MM * r.sites
-    return ROW_KERNEL.get(r.name, r.name), 1, r.nbytes
+    if r.name in ROW_KERNEL_FIXED:
+        return ROW_KERNEL_FIXED[r.name], 1, r.nbytes
+    if r.name not in ROW_TREE:
+        return r.name, 1, r.nbytes
+    tree, math, prec, adj = ROW_TREE[r.name]
+    v = tuned_variant if tuned_variant is not None else ROW_DEFAULT_VARIANT.get(r.name, 1)
+    if adj and v >= 10:
+        return ADJ_KERNEL[v - 10].format(t=T_MM, m="MathDF"), 2, B_ADJ_MM * r.sites
+    names = ADJ_KERNEL if adj else FWD_KERNEL
+    return names[v].format(t=tree, m=math, p=prec), 1, r.nbytes
 
 
 def dist_env():
@@ -1006,7 +1024,7 @@ def main():
                     help="skip the library's autotuner (by default it picks each row's launch "
                          "shape and data movement during setup, outside the timed region)")
     ap.add_argument("--pipeline", default="auto",
-                    choices=["auto", "plain", "tma", "tma_leaf", "tma_ring"],
+                    choices=["auto", "plain", "tma", "tma_leaf", "tma_ring", "tma_pair"],
                     help="data movement of FP64-storage kernels (default: the library's choice)")
     args = ap.parse_args()
     dims = tuple(int(x) for x in args.dims.split(","))
@@ -1055,7 +1073,8 @@ def main():
             print(json.dumps(line))
         return 0
     su3s.set_pipeline({"auto": su3s.PIPE_AUTO, "plain": su3s.PIPE_PLAIN, "tma": su3s.PIPE_TMA,
-                       "tma_leaf": su3s.PIPE_TMA_LEAF, "tma_ring": su3s.PIPE_TMA_RING}[args.pipeline])
+                       "tma_leaf": su3s.PIPE_TMA_LEAF, "tma_ring": su3s.PIPE_TMA_RING,
+                       "tma_pair": su3s.PIPE_TMA_PAIR}[args.pipeline])
     stream = torch.cuda.Stream()
     with_host = not args.no_e2e
     e2e_skip = None

@@ -318,7 +318,13 @@ int su3s_set_launch(const su3s_field* dest, const su3s_expr* e, int math, int th
  *    3  TMA-staged through a ring of three buffers per warp, for trees that
  *       read every object once per tile (others use their default): reading
  *       the object at position j of the tile's read order hands its buffer to
- *       position j + 3, of this tile or of the warp's next one.
+ *       position j + 3, of this tile or of the warp's next one;
+ *    4  TMA-staged two tiles at a time, two sites per lane: each warp stages
+ *       two 32-site tiles and every FP32 operation of SU3S_MATH_DF32 is one
+ *       packed instruction over the same real of two sites; for products of
+ *       two distinct matrix leaves (either may be an adjoint), sums and
+ *       differences of two such products over four distinct leaves, and the
+ *       reverse mode of such a product (others use their default).
  * All modes give bitwise identical results.  Staging needs 32 sites of a
  * component to be contiguous (SOA, or AOSOA with block >= 32); otherwise plain
  * loads are used.  EINVAL for other values. */
@@ -343,7 +349,7 @@ int su3s_device_error(int* code, void* stream);
 int su3s_selftest_bounded_wait(uint32_t polls, int64_t* cycles, void* stream);
 
 /* Autotune the launch geometry for `e` into `dest`: times each candidate
- * (data movement 0..3 as for su3s_set_pipeline, threads 64..256, full or
+ * (data movement 0..4 as for su3s_set_pipeline, threads 64..256, full or
  * grid-stride grids) with CUDA events on `stream` (synchronising it; dest is
  * overwritten, so a dest that is one of the leaves changes that leaf), keeps
  * the fastest for later su3s_eval calls and reports it in

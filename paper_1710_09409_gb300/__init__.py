@@ -146,14 +146,14 @@ def set_default_math(math):
     _check(load().su3s_set_default_math(math))
 
 
-PIPE_AUTO, PIPE_PLAIN, PIPE_TMA, PIPE_TMA_LEAF, PIPE_TMA_RING = -1, 0, 1, 2, 3
+PIPE_AUTO, PIPE_PLAIN, PIPE_TMA, PIPE_TMA_LEAF, PIPE_TMA_RING, PIPE_TMA_PAIR = -1, 0, 1, 2, 3, 4
 
 
 def set_pipeline(mode):
     """-1 the library's choice, 0 plain loads, 1 TMA-staged tiles, 2 TMA-staged
-    per leaf, 3 TMA-staged through a ring of buffers (FP64 storage; layouts
-    that keep 32 sites contiguous; trees without a ring kernel use their
-    default)."""
+    per leaf, 3 TMA-staged through a ring of buffers, 4 TMA-staged two tiles at
+    a time with two sites per lane (FP64 storage; layouts that keep 32 sites
+    contiguous; trees without a kernel of that mode use their default)."""
     _check(load().su3s_set_pipeline(mode))
 
 

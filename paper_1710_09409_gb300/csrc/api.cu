@@ -182,7 +182,8 @@ static int staged_occupancy(const void* kernel, int threads, int warp_bytes) {
   if (it != cache.end()) return it->second;
   int n = 0;
   const size_t smem = (size_t)(threads / 32) * warp_bytes;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * warp_bytes);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       8 * warp_bytes < smem_optin() ? 8 * warp_bytes : smem_optin());
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1)
     n = 1;
   cache[key] = n;
@@ -214,10 +215,13 @@ int plan_launch(const EvalEntry* e, int64_t nvec, int nmu, bool tma_ok, Launch* 
   }
   if (variant > 0) {
     int threads = g.threads > 0 ? g.threads : 128;
-    if (variant >= 2 && threads > 128) threads = 128;  // per-leaf / ring kernels: at most 4 warps
+    if ((variant == 2 || variant == 3) && threads > 128) threads = 128;  // per-leaf / ring: <= 4 warps
+    // at most the warps whose buffers fit one block's shared memory
+    while (threads > 32 && (threads / 32) * e->warp_bytes[variant] > smem_optin()) threads -= 32;
     const int occ = staged_occupancy(e->kernel[variant], threads, e->warp_bytes[variant]);
     const int per_sm = g.bps > 0 && g.bps < occ ? g.bps : occ;
-    const int64_t ntiles = nvec / 32, wpb = threads / 32;
+    // warps take 32-site tiles, or units of two tiles (two sites per lane)
+    const int64_t ntiles = variant == 4 ? (nvec / 32 + 1) / 2 : nvec / 32, wpb = threads / 32;
     int64_t nb = ((int64_t)per_sm * sm_count() + nmu - 1) / nmu;
     const int64_t need = (ntiles + wpb - 1) / wpb;
     if (nb > need) nb = need;
@@ -918,7 +922,7 @@ static int tune_entry(const EvalEntry* ent, const void* params, int64_t nvec, in
   for (int var = 0; var < (tma ? kNumVariants : 1) && rc == SU3S_OK; ++var) {
     if (!ent->fn[var]) continue;
     for (int th : th_c) {
-      if (var >= 2 && th > 128) continue;  // per-leaf / ring kernels take at most 4 warps
+      if ((var == 2 || var == 3) && th > 128) continue;  // per-leaf / ring: at most 4 warps
       for (int bps : bps_c) {
         set_geometry(ent->kernel[0], nvec, nmu, th, bps, var);
         Launch L;
@@ -975,7 +979,7 @@ SU3S_EXPORT int su3s_tune(su3s_field* dest, const su3s_expr* e, int math, void* 
 }
 
 SU3S_EXPORT int su3s_set_pipeline(int mode) {
-  if (mode < -1 || mode > 3) return fail(SU3S_EINVAL, "pipeline mode must be -1, 0, 1, 2 or 3");
+  if (mode < -1 || mode > 4) return fail(SU3S_EINVAL, "pipeline mode must be -1, 0, 1, 2, 3 or 4");
   g_pipeline_pref.store(mode, std::memory_order_relaxed);
   return ok();
 }

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <type_traits>
 
 #include "dev_expr.cuh"
 #include "dev_field.cuh"
@@ -1202,6 +1203,20 @@ cudaError_t launch_adjoint(const void* params, dim3 grid, dim3 block, cudaStream
   return cudaGetLastError();
 }
 
+// Largest dynamic shared memory a block may opt into on the current device.
+inline int smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        n <= 0)
+      n = 48 * 1024;
+    v = n;
+  }
+  return v;
+}
+
 // Dynamic shared memory of a TMA-staged launch: one tile buffer and one
 // barrier per warp.
 inline size_t tma_smem(int tile_bytes, dim3 block) {
@@ -1366,25 +1381,66 @@ struct IsLeafProduct<Mul<X, Y>> {
       BX::is_leaf && BY::is_leaf && SlotOf<BX>::value != SlotOf<BY>::value;
 };
 
+}  // namespace su3s
+
+#include "dev_pairs.cuh"
+
+namespace su3s {
+
 template <class Tree, class M, int PREC, bool GRAD>
 constexpr DefaultGeo default_geometry() {
   // With one tensor copy per object, whole-tile staging is the fastest data
-  // movement for every FP64 tree measured, in both FP64-accurate arithmetics.
-  // Forward products of two leaves run best in small blocks, about 8 warps
-  // per SM (16 for matrix times vector); the rest with the most that fit.
+  // movement for every FP64 tree measured, in both FP64-accurate arithmetics,
+  // except the reverse mode of a product of two matrix leaves in the pair
+  // arithmetic: two sites per lane.  Forward products of two leaves run best
+  // in small blocks, about 8 warps per SM (16 for matrix times vector); the
+  // rest with the most that fit.
   if constexpr (M::kScaled) return DefaultGeo{1, 128, 0};
+  else if constexpr (GRAD && pair_adjoint_ok<Tree, M>()) return DefaultGeo{4, 256, 0};
   else if constexpr (!GRAD && PREC == P_F64 && IsLeafProduct<Tree>::value)
     return Tree::kind == KV ? DefaultGeo{1, 64, 8} : DefaultGeo{1, 64, 4};
   else return DefaultGeo{1, 256, 0};
 }
 
+template <class Tree>
+cudaError_t launch_eval_pair(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int S = PairEvalLayout<Tree>::STRIDE;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_eval_pair<Tree>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * S < smem_optin() ? 8 * S : smem_optin());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_eval_pair<Tree><<<grid, block, (block.x / 32) * S, st>>>(*static_cast<const KParams*>(params));
+  return cudaGetLastError();
+}
+
+template <class Tree>
+cudaError_t launch_adjoint_pair(const void* params, dim3 grid, dim3 block, cudaStream_t st) {
+  constexpr int S = PairAdjLayout::STRIDE;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_pair<Tree>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * S < smem_optin() ? 8 * S : smem_optin());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_adjoint_pair<Tree><<<grid, block, (block.x / 32) * S, st>>>(*static_cast<const GParams*>(params));
+  return cudaGetLastError();
+}
+
 // Kernel variants of one tree: 0 plain loads, 1 TMA-staged eagerly (whole
 // tile), 2 TMA-staged lazily (per leaf), 3 TMA-staged through a ring of
-// buffers (trees that read each object once).  1-3 exist for FP64 storage.
+// buffers (trees that read each object once), 4 TMA-staged two tiles at a
+// time with two sites per lane (the pair arithmetic on products of matrix
+// leaves).  1-4 exist for FP64 storage.
 struct Variants {
-  LaunchFn fn[4];
-  const void* kernel[4];
-  int warp_bytes[4];  // shared memory per warp (0 for plain loads)
+  LaunchFn fn[5];
+  const void* kernel[5];
+  int warp_bytes[5];  // shared memory per warp (0 for plain loads)
   int default_variant;
   int default_threads;  // 0: library default
   int default_bps;
@@ -1409,6 +1465,11 @@ void reg_eval(int math) {
       v.kernel[3] = (const void*)&k_eval_ring<Tree, M, PREC>;
       v.warp_bytes[3] = RingLayout<Tree, PREC, false>::STRIDE;
     }
+    if constexpr (pair_eval_ok<Tree, M, PREC>()) {
+      v.fn[4] = &launch_eval_pair<Tree>;
+      v.kernel[4] = (const void*)&k_eval_pair<Tree>;
+      v.warp_bytes[4] = PairEvalLayout<Tree>::STRIDE;
+    }
     constexpr DefaultGeo g = default_geometry<Tree, M, PREC, false>();
     v.default_variant = g.variant;
     v.default_threads = g.threads;
@@ -1432,6 +1493,11 @@ void reg_adjoint(int math) {
     v.fn[3] = &launch_adjoint_ring<Tree, M>;
     v.kernel[3] = (const void*)&k_adjoint_ring<Tree, M>;
     v.warp_bytes[3] = RingLayout<Tree, P_F64, true>::STRIDE;
+  }
+  if constexpr (pair_adjoint_ok<Tree, M>()) {
+    v.fn[4] = &launch_adjoint_pair<Tree>;
+    v.kernel[4] = (const void*)&k_adjoint_pair<Tree>;
+    v.warp_bytes[4] = PairAdjLayout::STRIDE;
   }
   constexpr DefaultGeo g = default_geometry<Tree, M, P_F64, true>();
   v.default_variant = g.variant;

@@ -65,22 +65,29 @@ struct df {
 };
 
 // FP64 bit pattern (lo32, hi32) -> (xh, xl).  No FP64 instruction.
-__device__ __forceinline__ df df_split_bits(uint32_t lo32, uint32_t hi32) {
+//
+// Integer part of the split: hb = the bits of xh, m = the low 29 mantissa
+// bits as an FP32 value (xl = m * 2^(E-52), with E the exponent of xh).
+__device__ __forceinline__ void df_split_head(uint32_t lo32, uint32_t hi32, uint32_t& hb, float& m) {
   // rebias 1023 -> 127; exponents below 2^-126 collapse to 0 (fused add + max)
   const uint32_t w = (uint32_t)__viaddmax_s32((int)(hi32 & 0x7FFFFFFFu), -0x38000000, 0);
-  uint32_t t = __funnelshift_l(lo32, w, 3);  // exponent + top 23 fraction bits
-  uint32_t hb = t | (hi32 & 0x80000000u);
-  float xh = __uint_as_float(hb);
-  float m = __uint2float_rn(lo32 & 0x1FFFFFFFu);                        // low 29 bits
-  float pw = __fmul_rn(__uint_as_float(hb & 0xFF800000u), 0x1p-52f);    // +-2^(E-52)
-  return df{xh, __fmul_rn(m, pw)};
+  const uint32_t t = __funnelshift_l(lo32, w, 3);  // exponent + top 23 fraction bits
+  hb = t | (hi32 & 0x80000000u);
+  m = __uint2float_rn(lo32 & 0x1FFFFFFFu);         // low 29 bits
 }
 
-// (S, lo) with |lo| << |S| (not necessarily normalised) -> FP64.
-__device__ __forceinline__ double df_to_double(float S, float lo) {
-  float s = __fadd_rz(S, lo);          // toward zero: the remainder shares s's sign
-  float z = __fsub_rn(s, S);
-  float e = __fsub_rn(lo, z);
+// The split itself.
+__device__ __forceinline__ df df_split_bits(uint32_t lo32, uint32_t hi32) {
+  uint32_t hb;
+  float m;
+  df_split_head(lo32, hi32, hb, m);
+  float pw = __fmul_rn(__uint_as_float(hb & 0xFF800000u), 0x1p-52f);    // +-2^(E-52)
+  return df{__uint_as_float(hb), __fmul_rn(m, pw)};
+}
+
+// The FP64 bit pattern of s + e, s a sum rounded toward zero and e its exact
+// remainder (same sign as s, below one unit of s's last place).
+__device__ __forceinline__ double df_assemble(float s, float e) {
   uint32_t fs = __float_as_uint(s);
   uint32_t fa = fs & 0x7FFFFFFFu;
   uint32_t sg = fs & 0x80000000u;
@@ -90,6 +97,14 @@ __device__ __forceinline__ double df_to_double(float S, float lo) {
   hiw = fa ? hiw : sg;
   uint32_t low = fs * 0x20000000u + low29;  // (fs << 29) | low29; both zero when s == 0
   return __hiloint2double((int)hiw, (int)low);
+}
+
+// (S, lo) with |lo| << |S| (not necessarily normalised) -> FP64.
+__device__ __forceinline__ double df_to_double(float S, float lo) {
+  float s = __fadd_rz(S, lo);          // toward zero: the remainder shares s's sign
+  float z = __fsub_rn(s, S);
+  float e = __fsub_rn(lo, z);
+  return df_assemble(s, e);
 }
 
 // Normalise (S, lo) into a pair usable as an operand: Fast2Sum.

@@ -60,8 +60,9 @@ int check_same_shape(const su3s_field* a, const su3s_field* b, bool same_prec);
 int sm_count();
 
 // kernel registry
-// Variants: 0 plain loads, 1 TMA-staged whole tile, 2 TMA-staged per leaf.
-constexpr int kNumVariants = 4;
+// Variants: 0 plain loads, 1 TMA-staged whole tile, 2 TMA-staged per leaf,
+// 3 TMA-staged ring, 4 TMA-staged two tiles with two sites per lane.
+constexpr int kNumVariants = 5;
 struct EvalEntry {
   cudaError_t (*fn[kNumVariants])(const void*, dim3, dim3, cudaStream_t);
   const void* kernel[kNumVariants];

@@ -259,9 +259,9 @@ def test_package_never_reaches_the_oracle():
 
 
 def test_pipeline_modes(L):
-    for mode in (-1, 0, 1, 2, 3):
+    for mode in (-1, 0, 1, 2, 3, 4):
         assert L.su3s_set_pipeline(mode) == 0
-    assert L.su3s_set_pipeline(4) == 1
+    assert L.su3s_set_pipeline(5) == 1
     assert L.su3s_set_pipeline(-2) == 1
     assert L.su3s_set_pipeline(-1) == 0
 

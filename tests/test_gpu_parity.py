@@ -159,7 +159,8 @@ def test_dest_aliases_leaf_every_pipeline(su3s):
     f = lattice_fields(dims, SEED + 12, names=("a", "b", "c", "d"))
     ref1, ref3 = oracle.eval_tree(E1, f), oracle.eval_tree(E3, f)
     try:
-        for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF, su3s.PIPE_TMA_RING):
+        for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF, su3s.PIPE_TMA_RING,
+                     su3s.PIPE_TMA_PAIR):
             su3s.set_pipeline(mode)
             F = {n: upload(su3s, lat, f[n]) for n in "abcd"}
             e1 = F["a"] * F["b"] + F["c"] * F["d"]
@@ -756,7 +757,8 @@ def test_tma_staging_is_bitwise_identical(su3s, lay, math):
     """The TMA-staged kernels (bulk copies into shared memory, one 32-site tile
     per warp: whole tile, per leaf, or through a ring of buffers) and the
     plain-load kernels run the same arithmetic per site."""
-    PIPES = (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF, su3s.PIPE_TMA_RING)
+    PIPES = (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF, su3s.PIPE_TMA_RING,
+             su3s.PIPE_TMA_PAIR)
     dims = (8, 8, 8, 9)
     lat = su3s.Lattice(dims)
     f = lattice_fields(dims, SEED, nmu=4, names=("a", "b", "c", "d", "w"))
@@ -826,6 +828,60 @@ def test_ring_staging_over_many_tiles_per_warp(su3s):
         su3s.set_pipeline(su3s.PIPE_AUTO)
     assert su3s.device_error() == 0
 
+
+
+@pytest.mark.parametrize("dims,nmu,lay", [((17, 17, 17, 17), 1, LAYOUTS[2]),
+                                          ((6, 6, 6, 6), 4, LAYOUTS[2]),
+                                          ((3, 3, 3, 3), 1, LAYOUTS[0])],
+                         ids=["17^4-aosoa32", "6^4-nmu4-aosoa32", "3^4-soa"])
+def test_pair_kernels_bitwise_over_odd_tiles(su3s, dims, nmu, lay):
+    """The two-sites-per-lane kernels (mode 4: a warp takes two 32-site tiles
+    per step, every pair-arithmetic operation packed over the two sites) give
+    the plain-load kernels' results bit for bit.  With 32-site blocks the
+    lattices have an odd number of tiles, so the last step has one; 17^4 with
+    152 one-warp blocks gives each warp ~9 steps; 3^4 is one step of padded
+    sites.  Every adjoint placement in a product, a sum and a difference of
+    products, and the reverse mode with both gradients and with one."""
+    lat = su3s.Lattice(dims)
+    if lay[2] == 32:
+        assert ((np.prod(dims) + 31) // 32) % 2 == 1
+    f = lattice_fields(dims, SEED + 13, nmu=nmu, names=("a", "b", "c", "d", "w"))
+    F = {n: upload(su3s, lat, f[n], nmu=nmu, layout=lay[1], block=lay[2]) for n in "abcdw"}
+    a, b, c, d, w = (F[n] for n in "abcdw")
+    exprs = [a * b, a.adj() * b, a * b.adj(), a.adj() * b.adj(), a * b + c * d, a * b - c * d]
+    try:
+        for e in exprs:
+            outs = []
+            for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA_PAIR):
+                su3s.set_pipeline(mode)
+                z = a.like()
+                if dims[0] == 17:
+                    su3s.set_launch(z, e, 32, 1)    # 152 one-warp blocks
+                su3s.evaluate(z, e)
+                outs.append(z.download())
+            assert np.array_equal(outs[0], outs[1])
+        for e in (a * b, a.adj() * b, a * b.adj()):
+            for want in ((True, True), (True, False), (False, True)):
+                gs = []
+                for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA_PAIR):
+                    su3s.set_pipeline(mode)
+                    g = [a.like() if k else None for k in want]
+                    su3s.eval_adjoint(e, w, g)
+                    gs.append([x.download() for x in g if x is not None])
+                for x, y in zip(*gs):
+                    assert np.array_equal(x, y)
+    finally:
+        su3s.set_pipeline(su3s.PIPE_AUTO)
+    assert su3s.device_error() == 0
+    # and against the oracle
+    ref = oracle.eval_tree(E1, f)
+    su3s.set_pipeline(su3s.PIPE_TMA_PAIR)
+    try:
+        z = a.like()
+        su3s.evaluate(z, a * b + c * d)
+    finally:
+        su3s.set_pipeline(su3s.PIPE_AUTO)
+    assert np.abs(z.download() - ref).max() < 2 * TOL
 
 # ---------------------------------------------------------- tuning
 def test_launch_geometry_does_not_change_results(su3s):

@@ -86,7 +86,8 @@ def fields(su3s, dims, arrs, kinds=None, nmu=1, layout=0, block=64):
 
 
 @pytest.mark.parametrize("math", GUARDED, ids=GUARDED_IDS)
-@pytest.mark.parametrize("pipeline", [-1, 0, 1, 2, 3], ids=["auto", "plain", "tile", "leaf", "ring"])
+@pytest.mark.parametrize("pipeline", [-1, 0, 1, 2, 3, 4],
+                         ids=["auto", "plain", "tile", "leaf", "ring", "pair"])
 def test_product_with_special_inputs(su3s, math, pipeline):
     f = lattice_fields(DIMS, SEED, names=("a", "b"))
     trips = plant(f["a"], 3) + plant(f["b"], 200)
@@ -120,13 +121,18 @@ def test_in_place_product_reads_its_inputs_before_the_fallback(su3s, math):
 
 @pytest.mark.parametrize("math", GUARDED, ids=GUARDED_IDS)
 @pytest.mark.parametrize("layout,block", [(0, 64), (1, 32), (1, 4)], ids=["soa", "aosoa32", "aosoa4"])
-def test_fused_sum_of_products(su3s, math, layout, block):
+@pytest.mark.parametrize("pipeline", [-1, 4], ids=["auto", "pair"])
+def test_fused_sum_of_products(su3s, math, layout, block, pipeline):
     f = lattice_fields(DIMS, SEED + 2, names=("a", "b", "c", "d"))
     plant(f["a"], 5)
     plant(f["d"], 150)
     F = fields(su3s, DIMS, f, layout=layout, block=block)
     z = F["a"].like()
-    su3s.evaluate(z, F["a"] * F["b"] + F["c"] * F["d"], math)
+    su3s.set_pipeline(pipeline)
+    try:
+        su3s.evaluate(z, F["a"] * F["b"] + F["c"] * F["d"], math)
+    finally:
+        su3s.set_pipeline(-1)
     scale = site_scale(f["a"], f["b"]) + site_scale(f["c"], f["d"])
     assert_ieee(z.download(), oracle.eval_tree(E1, f), scale)
 
@@ -184,7 +190,7 @@ def test_interpreter_tree(su3s, math):
 
 
 @pytest.mark.parametrize("math", GUARDED, ids=GUARDED_IDS)
-@pytest.mark.parametrize("pipeline", [-1, 0, 2, 3], ids=["auto", "plain", "leaf", "ring"])
+@pytest.mark.parametrize("pipeline", [-1, 0, 2, 3, 4], ids=["auto", "plain", "leaf", "ring", "pair"])
 @pytest.mark.parametrize("tree", ["ab", "e1"])
 def test_reverse_mode_with_special_inputs(su3s, math, pipeline, tree):
     names = ("a", "b") if tree == "ab" else ("a", "b", "c", "d")
