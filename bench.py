@@ -98,10 +98,11 @@ ROW_DEFAULT_VARIANT = {"A9 adjoint of z=a*b": 4, "A9 adjoint of z=a*b+c*d": 14}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel on a 32^4 lattice (1,048,576 sites; the batch row: its 64 fixed
-# lattices), from one ncu capture of the benchmark step as it stands (default
-# launches, profiles/top_kernels_32x4.md): (bytes, algorithmic bytes of that
-# launch); scaled to the benchmark's volume in proportion to the algorithmic
-# bytes.  A kernel missing here reports traffic null.
+# lattices), from one ncu capture of that kernel in the benchmark's rows as
+# they stand (default launches, one launch after the warm-up): (bytes,
+# algorithmic bytes of that launch); scaled to the benchmark's volume in
+# proportion to the algorithmic bytes.  A kernel missing here reports traffic
+# null.
 TRAFFIC_32 = {
     "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 0>": (413.0 * 1e6, 452984832),
     "k_eval_tma<Mul<LM<0>, LV<1>>, MathDF, 0>": (228.3 * 1e6, 251658240),
@@ -111,6 +112,7 @@ TRAFFIC_32 = {
     "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 4>": (260.5 * 1e6, 301989888),
     "k_batch_tma<MathDF, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>": (4603.0 * 1e6, 4622376960),
     "k_adjoint_tma<Mul<LM<0>, LM<1>>, MathDF>": (700.8 * 1e6, 754974720),
+    "k_adjoint_pair<Mul<LM<0>, LM<1>>>": (703.8 * 1e6, 754974720),
 }
 
 
