@@ -59,14 +59,14 @@ struct Store<P_F64> {
   __device__ static __forceinline__ void load(const void* base, int64_t e, typename M::R* re,
                                               typename M::R* im) {
     uint4 v = ld16((const char*)base + e * 16);
-    re[0] = M::from_bits(v.x, v.y);
-    im[0] = M::from_bits(v.z, v.w);
+    split_complex<M>(v, re[0], im[0]);
   }
   // from accumulators
   template <class M>
   __device__ static __forceinline__ void store_acc(void* base, int64_t e, const typename M::A* re,
                                                    const typename M::A* im) {
-    double r = M::to_f64(re[0]), i = M::to_f64(im[0]);
+    double r, i;
+    complex_to_f64<M>(re[0], im[0], r, i);
     st16((char*)base + e * 16, make_uint4((uint32_t)__double2loint(r), (uint32_t)__double2hiint(r),
                                           (uint32_t)__double2loint(i), (uint32_t)__double2hiint(i)));
   }

@@ -92,8 +92,7 @@ __device__ __forceinline__ void load_obj(const FieldDesc& f, int64_t s, int mu, 
         static_assert(VPS == 1, "guarded arithmetics read FP64 storage");
         const uint4 v = ld16((const char*)f.ptr + (b + c * f.s_c) * 16);
         gm[c] = guard_max(0u, v.y, v.w);
-        re[0] = M::from_bits(v.x, v.y);
-        im[0] = M::from_bits(v.z, v.w);
+        split_complex<M>(v, re[0], im[0]);
       } else {
         St::template load<M>(f.ptr, b + c * f.s_c, re, im);
       }
@@ -455,8 +454,7 @@ __device__ __forceinline__ void read_obj(const unsigned char* src, int lane, C& 
     for (int c = 0; c < NC; ++c) {
       const uint4 v = reinterpret_cast<const uint4*>(src + c * 512)[lane];
       if constexpr (M::kGuard) gm[c] = guard_max(0u, v.y, v.w);
-      ctx.leaf[slot][2 * c] = M::from_bits(v.x, v.y);
-      ctx.leaf[slot][2 * c + 1] = M::from_bits(v.z, v.w);
+      split_complex<M>(v, ctx.leaf[slot][2 * c], ctx.leaf[slot][2 * c + 1]);
     }
     if constexpr (M::kGuard) ctx.gmax = max(ctx.gmax, guard_reduce<NC>(gm));
     M::template normalize_obj<2 * NC>(ctx.leaf[slot]);

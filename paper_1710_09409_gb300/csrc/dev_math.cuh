@@ -57,6 +57,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace su3s {
 
 // ----------------------------------------------------------------- helpers
@@ -201,6 +203,7 @@ struct MathDF {
   static constexpr bool kScaled = false;
   static constexpr bool kPaired = true;   // complex products in packed (re, im) lanes
   static constexpr bool kGuard = true;    // FP32 exponent range: sites are range-checked
+  static constexpr bool kPackSplit = true;  // complex inputs split, outputs converted, in pairs
   __device__ static __forceinline__ R from_bits(uint32_t lo, uint32_t hi) {
     return df_split_bits(lo, hi);
   }
@@ -284,6 +287,16 @@ struct MathDF {
 // instructions save.  Results are identical to MathDF's.
 struct MathDFScalar : MathDF {
   static constexpr bool kPaired = false;
+};
+
+// The same arithmetic with every FP64 input split and every output converted
+// one real at a time (MathDF packs the two reals of a complex element: the
+// same values).  Measured faster for the batch kernel and the Wilson term,
+// whose schedules lost more to the packed operations' register pairs than the
+// packing saved (64 lattices: 5,922 against 5,802 GB/s; Wilson term at 48^4:
+// 1,848 against 1,799).
+struct MathDFUnpacked : MathDF {
+  static constexpr bool kPackSplit = false;
 };
 
 // --------------------------------------------- MathDF, packed (re, im) lanes
@@ -585,5 +598,82 @@ struct MathF32 {
     a = (SG > 0) ? __fadd_rn(a, b) : __fsub_rn(a, b);
   }
 };
+
+// ------------------------------------------ complex elements, two reals
+// Packed product, used only where it feeds another product: a packed
+// multiply feeding a packed add is not kept apart from it (see f2_mul).
+__device__ __forceinline__ float2 f2_mul_packed(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_add_rz(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rz.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// df_split_bits of two FP64 values (lane 0: (lo0, hi0), lane 1: (lo1, hi1)),
+// its two FP32 multiplies packed.
+__device__ __forceinline__ df2 df2_split(uint32_t lo0, uint32_t hi0, uint32_t lo1, uint32_t hi1) {
+  uint32_t hb0, hb1;
+  float m0, m1;
+  df_split_head(lo0, hi0, hb0, m0);
+  df_split_head(lo1, hi1, hb1, m1);
+  const float2 pw = f2_mul_packed(make_float2(__uint_as_float(hb0 & 0xFF800000u),
+                                              __uint_as_float(hb1 & 0xFF800000u)),
+                                  make_float2(0x1p-52f, 0x1p-52f));  // +-2^(E-52)
+  return df2{make_float2(__uint_as_float(hb0), __uint_as_float(hb1)),
+             f2_mul_packed(make_float2(m0, m1), pw)};
+}
+
+// df_to_double of two accumulators (lanes of a DAcc2), its FP32 operations packed.
+__device__ __forceinline__ void df2_to_double(const DAcc2& a, double& d0, double& d1) {
+  const float2 s = f2_add_rz(a.S, a.lo);  // toward zero: the remainder shares s's sign
+  const float2 z = f2_sub(s, a.S);
+  const float2 e = f2_sub(a.lo, z);
+  d0 = df_assemble(s.x, e.x);
+  d1 = df_assemble(s.y, e.y);
+}
+
+// Whether M splits and converts complex elements in packed pairs.
+template <class M>
+__host__ __device__ constexpr bool pack_split() {
+  if constexpr (std::is_base_of<MathDF, M>::value) return M::kPackSplit;
+  else return false;
+}
+
+// One complex element (16 bytes: re lo, re hi, im lo, im hi) into the
+// arithmetic's two reals.  The pair arithmetic splits both at once with its
+// multiplies packed over (re, im); each lane repeats df_split_bits, so the
+// values are those of from_bits.
+template <class M>
+__device__ __forceinline__ void split_complex(uint4 v, typename M::R& re, typename M::R& im) {
+  if constexpr (pack_split<M>()) {
+    const df2 p = df2_split(v.x, v.y, v.z, v.w);
+    re = df{p.h.x, p.l.x};
+    im = df{p.h.y, p.l.y};
+  } else {
+    re = M::from_bits(v.x, v.y);
+    im = M::from_bits(v.z, v.w);
+  }
+}
+
+// The FP64 values of a complex output's two accumulators (packed for the pair
+// arithmetic, with to_f64's values).
+template <class M>
+__device__ __forceinline__ void complex_to_f64(const typename M::A& re, const typename M::A& im,
+                                               double& r, double& i) {
+  if constexpr (pack_split<M>()) {
+    df2_to_double(DAcc2{make_float2(re.S, im.S), make_float2(re.lo, im.lo)}, r, i);
+  } else {
+    r = M::to_f64(re);
+    i = M::to_f64(im);
+  }
+}
 
 }  // namespace su3s

@@ -30,43 +30,14 @@ using dp = df2;
 // accumulator of one real of the two sites (MathDF's DAcc, lane-wise)
 using dpa = DAcc2;
 
-// Packed product, used only where it feeds another product: a packed
-// multiply feeding a packed add is not kept apart from it (see f2_mul).
-__device__ __forceinline__ float2 f2_mul_packed(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 f2_add_rz(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "add.rz.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-
-// df_split_bits of two FP64 values, its two FP32 multiplies packed.
+// df_split_bits of two FP64 values (the same real of the two sites).
 __device__ __forceinline__ dp dp_split(uint32_t lo0, uint32_t hi0, uint32_t lo1, uint32_t hi1) {
-  uint32_t hb0, hb1;
-  float m0, m1;
-  df_split_head(lo0, hi0, hb0, m0);
-  df_split_head(lo1, hi1, hb1, m1);
-  const float2 pw = f2_mul_packed(make_float2(__uint_as_float(hb0 & 0xFF800000u),
-                                              __uint_as_float(hb1 & 0xFF800000u)),
-                                  make_float2(0x1p-52f, 0x1p-52f));  // +-2^(E-52)
-  return dp{make_float2(__uint_as_float(hb0), __uint_as_float(hb1)),
-            f2_mul_packed(make_float2(m0, m1), pw)};
+  return df2_split(lo0, hi0, lo1, hi1);
 }
 
-// df_to_double of both lanes, its three FP32 operations packed.
+// df_to_double of both lanes.
 __device__ __forceinline__ void dp_to_double(const dpa& a, double& d0, double& d1) {
-  const float2 s = f2_add_rz(a.S, a.lo);  // toward zero: the remainder shares s's sign
-  const float2 z = f2_sub(s, a.S);
-  const float2 e = f2_sub(a.lo, z);
-  d0 = df_assemble(s.x, e.x);
-  d1 = df_assemble(s.y, e.y);
+  df2_to_double(a, d0, d1);
 }
 
 __device__ __forceinline__ float2 f2_neg(float2 a) { return make_float2(-a.x, -a.y); }

@@ -39,8 +39,7 @@ __device__ __forceinline__ void load_nc(const FieldDesc& f, int64_t s, int mu, t
   for (int c = 0; c < W / 2; ++c) {
     const uint4 v = __ldg(p + b + c * f.s_c);
     if constexpr (M::kGuard) g = guard_max(g, v.y, v.w);
-    out[2 * c] = M::from_bits(v.x, v.y);
-    out[2 * c + 1] = M::from_bits(v.z, v.w);
+    split_complex<M>(v, out[2 * c], out[2 * c + 1]);
   }
   M::template normalize_obj<W>(out);
 }
@@ -62,8 +61,7 @@ __device__ __forceinline__ void load_link(const FieldDesc& f, int64_t s, int mu,
       const int c = 3 * i + j;
       const uint4 v = __ldg(p + b + (dag ? 3 * j + i : c) * f.s_c);
       if constexpr (M::kGuard) g = guard_max(g, v.y, v.w);
-      out[2 * c] = M::from_bits(v.x, v.y);
-      out[2 * c + 1] = M::from_bits(v.z, v.w ^ sg);
+      split_complex<M>(make_uint4(v.x, v.y, v.z, v.w ^ sg), out[2 * c], out[2 * c + 1]);
     }
   M::template normalize_obj<18>(out);
 }

@@ -204,8 +204,7 @@ __device__ __forceinline__ void read_staged(const uint4* slot, int nt, int first
   for (int c = 0; c < W / 2; ++c) {
     const uint4 v = slot[(first + c) * nt];
     if constexpr (M::kGuard) gm = guard_max(gm, v.y, v.w);
-    out[2 * c] = M::from_bits(v.x, v.y);
-    out[2 * c + 1] = M::from_bits(v.z, v.w);
+    split_complex<M>(v, out[2 * c], out[2 * c + 1]);
   }
   M::template normalize_obj<W>(out);
 }
@@ -222,8 +221,8 @@ __device__ __forceinline__ void read_staged_link(const uint4* slot, int nt, bool
       for (int j = 0; j < 3; ++j) {
         const uint4 v = slot[(12 + 3 * j + i) * nt];
         if constexpr (M::kGuard) gm = guard_max(gm, v.y, v.w);
-        out[2 * (3 * i + j)] = M::from_bits(v.x, v.y);
-        out[2 * (3 * i + j) + 1] = M::from_bits(v.z, v.w ^ 0x80000000u);
+        split_complex<M>(make_uint4(v.x, v.y, v.z, v.w ^ 0x80000000u), out[2 * (3 * i + j)],
+                         out[2 * (3 * i + j) + 1]);
       }
     M::template normalize_obj<18>(out);
   } else {
@@ -361,7 +360,7 @@ SU3S_EXPORT int su3s_dslash(su3s_field* dest, const su3s_field* U, const su3s_fi
   if (psi->V == 0) return SU3S_OK;
   cudaError_t ce = m == MATH_F64  ? launch_dslash<MathF64>(dest, U, psi, st)
                    : m == MATH_FX ? launch_dslash<MathFX>(dest, U, psi, st)
-                                  : launch_dslash<MathDF>(dest, U, psi, st);
+                                  : launch_dslash<MathDFUnpacked>(dest, U, psi, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "Wilson hopping-term kernel launch");
   return SU3S_OK;
 }

@@ -73,8 +73,7 @@ __device__ __forceinline__ void i_load(const FieldDesc& f, int64_t s, int mu, ty
     for (int c = 0; c < W / 2; ++c) {
       const uint4 v = ld16((const char*)f.ptr + (b + c * f.s_c) * 16);
       if constexpr (M::kGuard) g = guard_max(g, v.y, v.w);
-      r[2 * c] = M::from_bits(v.x, v.y);
-      r[2 * c + 1] = M::from_bits(v.z, v.w);
+      split_complex<M>(v, r[2 * c], r[2 * c + 1]);
     }
   }
   M::template normalize_obj<W>(r);
