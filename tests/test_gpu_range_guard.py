@@ -191,8 +191,9 @@ def test_interpreter_tree(su3s, math):
 
 @pytest.mark.parametrize("math", GUARDED, ids=GUARDED_IDS)
 @pytest.mark.parametrize("pipeline", [-1, 0, 2, 3, 4], ids=["auto", "plain", "leaf", "ring", "pair"])
-@pytest.mark.parametrize("tree", ["ab", "e1"])
-def test_reverse_mode_with_special_inputs(su3s, math, pipeline, tree):
+@pytest.mark.parametrize("tree,split", [("ab", -1), ("e1", -1), ("e1", 0)],
+                         ids=["ab", "e1", "e1-fused"])
+def test_reverse_mode_with_special_inputs(su3s, math, pipeline, tree, split):
     names = ("a", "b") if tree == "ab" else ("a", "b", "c", "d")
     f = lattice_fields(DIMS, SEED + 6, names=names + ("w",))
     plant(f["a"], 21)
@@ -205,10 +206,12 @@ def test_reverse_mode_with_special_inputs(su3s, math, pipeline, tree):
         e, t = F["a"] * F["b"] + F["c"] * F["d"], E1
     grads = [F[n].like() for n in names]
     su3s.set_pipeline(pipeline)
+    su3s.set_adjoint_split(split)
     try:
         su3s.eval_adjoint(e, F["w"], grads, math)
     finally:
         su3s.set_pipeline(-1)
+        su3s.set_adjoint_split(-1)
     ref = oracle.eval_adjoint(t, leaves, f["w"])
     for n, g in zip(names, grads):
         others = [f[m] for m in names if m != n] + [f["w"]]
