@@ -117,6 +117,28 @@ __global__ void __launch_bounds__(256) k_batch_tma(const BItem* __restrict__ ite
     }
     phase ^= 1;
     ctx.gmax = p.gscal;
+    if constexpr (TwoProducts<Tree>::value) {
+      // the first product's leaves, the product, then the second's (as the
+      // whole-tile single-lattice kernel)
+      using TP = TwoProducts<Tree>;
+      typename M::A acc[1][W];
+      read_leaves_of<Tree, typename TP::P0, 0, P_F64, M>(buf, lane, ctx);
+      acc_into<typename TP::P0, M, true, 1>(ctx, acc[0]);
+      read_leaves_of<Tree, typename TP::P1, 0, P_F64, M>(buf, lane, ctx);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (in < end)
+        issue_tile<Tree, P_F64, false>(lane, items[Tn.item].k, nullptr, nullptr, Tn.s0, Tn.mu, buf, bar);
+      if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(ctx.gmax))) {
+        eval_site_f64<Tree, P_F64>(p, T.s0 + lane, T.mu);
+      } else {
+        mul_combine<M, TP::S1>(ctx, acc[0], (typename TP::P1*)nullptr);
+        store_obj<Tree::kind, P_F64, M, 1, W>(p.dst, T.s0 + lane, T.mu, acc);
+      }
+      T = Tn;
+      i = in;
+      continue;
+    }
     read_leaves<Tree, 0, P_F64, M>(buf, lane, ctx);
     fence_proxy_async_smem();
     __syncwarp();

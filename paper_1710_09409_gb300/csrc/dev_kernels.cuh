@@ -470,6 +470,44 @@ __device__ __forceinline__ void read_leaves(const unsigned char* buf, int lane, 
   }
 }
 
+// Sums and differences of two products over disjoint leaves (a*b + c*d): the
+// whole-tile kernels read the first product's leaves, evaluate it, and only
+// then read the second's (the tile's buffer is refilled once the last leaf is
+// read), so the two products' operands are never live together.  The
+// evaluation is acc_node's for such a sum: the first product into the
+// accumulators, the second combined (mul_combine).
+template <class X, class Y, int I>
+constexpr bool disjoint_leaves() {
+  if constexpr (I >= kMaxLeaves) return true;
+  else return (Count<X, I>::value == 0 || Count<Y, I>::value == 0) && disjoint_leaves<X, Y, I + 1>();
+}
+template <class T>
+struct TwoProducts {
+  static constexpr bool value = false;
+};
+template <class X, class Y, int SG>
+struct TwoProductsOf {
+  static constexpr bool value =
+      IsMulNode<X>::value && IsMulNode<Y>::value && disjoint_leaves<X, Y, 0>();
+  using P0 = X;
+  using P1 = Y;
+  static constexpr int S1 = SG;
+};
+template <class X, class Y>
+struct TwoProducts<Add<X, Y>> : TwoProductsOf<X, Y, 1> {};
+template <class X, class Y>
+struct TwoProducts<Sub<X, Y>> : TwoProductsOf<X, Y, -1> {};
+
+// Read the staged leaves of subtree Sub (this lane's site) into ctx.
+template <class Tree, class Sub, int I, int PREC, class M, class C>
+__device__ __forceinline__ void read_leaves_of(const unsigned char* buf, int lane, C& ctx) {
+  if constexpr (I < Tree::nleaf) {
+    if constexpr (Count<Sub, I>::value > 0)
+      read_obj<LeafKind<Tree, I>::value, PREC, M>(buf + LeafOff<Tree, PREC, I>::value, lane, ctx, I);
+    read_leaves_of<Tree, Sub, I + 1, PREC, M>(buf, lane, ctx);
+  }
+}
+
 template <class Tree, class M, int PREC>
 __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned char* smem) {
   constexpr int NL = Tree::nleaf;
@@ -501,10 +539,29 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
     }
     phase ^= 1;
     ctx.gmax = p.gscal;
+    const int64_t tn = t + wstride;
+    if constexpr (TwoProducts<Tree>::value) {
+      using TP = TwoProducts<Tree>;
+      typename M::A acc[1][W];
+      read_leaves_of<Tree, typename TP::P0, 0, PREC, M>(buf, lane, ctx);
+      acc_into<typename TP::P0, M, true, 1>(ctx, acc[0]);
+      read_leaves_of<Tree, typename TP::P1, 0, PREC, M>(buf, lane, ctx);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, nullptr, tn << 5, mu, buf, bar);
+      // the range is known once every leaf is read; nothing is stored yet
+      if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(ctx.gmax))) {
+        eval_site_f64<Tree, PREC>(p, (t << 5) + lane, mu);
+      } else {
+        mul_combine<M, TP::S1>(ctx, acc[0], (typename TP::P1*)nullptr);
+        store_obj<Tree::kind, PREC, M, 1, W>(p.dst, (t << 5) + lane, mu, acc);
+      }
+      t = tn;
+      continue;
+    }
     read_leaves<Tree, 0, PREC, M>(buf, lane, ctx);
     fence_proxy_async_smem();
     __syncwarp();
-    const int64_t tn = t + wstride;
     if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, nullptr, tn << 5, mu, buf, bar);
     // a tile with a site out of range runs all its sites in native FP64: the
     // decision is warp-uniform, so the hot path has no divergent branch
