@@ -87,7 +87,7 @@ ROW_TREE = {
     "A9 adjoint of z=a*b+c*d": (T_E1, "MathDFScalar", 0, True),
 }
 ROW_KERNEL_FIXED = {
-    "A8 batch 64 lattices z=a*b+c*d": "k_batch_tma<MathDFUnpacked, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>",
+    "A8 batch 64 lattices z=a*b+c*d": "k_batch_tma<MathDF, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>",
 }
 FWD_KERNEL = ["k_eval<{t}, {m}, {p}>", "k_eval_tma<{t}, {m}, {p}>", "k_eval_lazy<{t}, {m}, {p}>",
               "k_eval_ring<{t}, {m}, {p}>", "k_eval_pair<{t}>"]

@@ -176,7 +176,7 @@ static const void* batch_kernel(int tree) {
 static const void* batch_kernel(int math, int tree) {
   return math == MATH_F64  ? batch_kernel<MathF64>(tree)
          : math == MATH_FX ? batch_kernel<MathFX>(tree)
-                           : batch_kernel<MathDFUnpacked>(tree);
+                           : batch_kernel<MathDF>(tree);
 }
 
 // Staged persistent kernel of batch tree `tree` and its tile bytes per warp.
@@ -201,7 +201,7 @@ static const void* batch_kernel_tma(int tree, int* warp_bytes) {
 static const void* batch_kernel_tma(int math, int tree, int* warp_bytes) {
   return math == MATH_F64  ? batch_kernel_tma<MathF64>(tree, warp_bytes)
          : math == MATH_FX ? batch_kernel_tma<MathFX>(tree, warp_bytes)
-                           : batch_kernel_tma<MathDFUnpacked>(tree, warp_bytes);
+                           : batch_kernel_tma<MathDF>(tree, warp_bytes);
 }
 
 }  // namespace su3s

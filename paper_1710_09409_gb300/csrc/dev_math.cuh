@@ -291,10 +291,9 @@ struct MathDFScalar : MathDF {
 
 // The same arithmetic with every FP64 input split and every output converted
 // one real at a time (MathDF packs the two reals of a complex element: the
-// same values).  Measured faster for the batch kernel and the Wilson term,
-// whose schedules lost more to the packed operations' register pairs than the
-// packing saved (64 lattices: 5,922 against 5,802 GB/s; Wilson term at 48^4:
-// 1,848 against 1,799).
+// same values).  Measured faster for the Wilson term, whose schedule lost more
+// to the packed operations' register pairs than the packing saved (48^4:
+// 1,848 against 1,799 GB/s).
 struct MathDFUnpacked : MathDF {
   static constexpr bool kPackSplit = false;
 };
