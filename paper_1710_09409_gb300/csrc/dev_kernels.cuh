@@ -31,6 +31,31 @@ struct IsC12 {
 // (c, j, k) cyclic.
 template <class M>
 __device__ __forceinline__ void rebuild_row2(typename M::R* m) {
+  if constexpr (M::kPaired) {
+    // the pair arithmetic: the real and imaginary parts of each rebuilt element
+    // advance together in packed lanes, each lane repeating the scalar terms
+    // below in their order (re: +ajr bkr, -aji bki, -akr bjr, +aki bji; im:
+    // -ajr bki, -aji bkr, +akr bji, +aki bjr)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int j = (c + 1) % 3, k = (c + 2) % 3;
+      const df ajr = m[2 * j], aji = m[2 * j + 1], akr = m[2 * k], aki = m[2 * k + 1];
+      const df bjr = m[6 + 2 * j], bji = m[6 + 2 * j + 1];
+      const df bkr = m[6 + 2 * k], bki = m[6 + 2 * k + 1];
+      auto pr = [](df x0, bool n0, df x1, bool n1) {
+        return df2{make_float2(n0 ? -x0.h : x0.h, n1 ? -x1.h : x1.h),
+                   make_float2(n0 ? -x0.l : x0.l, n1 ? -x1.l : x1.l)};
+      };
+      DAcc2 a;
+      df2_first(a, pr(ajr, false, ajr, true), pr(bkr, false, bki, false));
+      df2_fma(a, pr(aji, true, aji, true), pr(bki, false, bkr, false));
+      df2_fma(a, pr(akr, true, akr, false), pr(bjr, false, bji, false));
+      df2_fma(a, pr(aki, false, aki, false), pr(bji, false, bjr, false));
+      m[12 + 2 * c] = df_norm(a.S.x, a.lo.x);
+      m[12 + 2 * c + 1] = df_norm(a.S.y, a.lo.y);
+    }
+    return;
+  }
   // fixed point: row 2 comes out at the scale of a product; the 18 reals are
   // renormalised together to one shared exponent
   typename M::A a[M::kScaled ? 18 : 1];
