@@ -53,6 +53,31 @@ __device__ __forceinline__ typename M::A neg_acc(const typename M::A& a) {
 template <class M>
 __device__ __forceinline__ void half_spinor(typename M::R* h, const typename M::R* u,
                                             const typename M::R* l, Phase P) {
+  if constexpr (M::kPaired) {
+    // the pair arithmetic: real and imaginary parts in packed lanes, each lane
+    // repeating MathDF::add's operations (the copy, then TwoSum of the
+    // leading parts with the tail gathered)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const df a = P.swap ? l[2 * c + 1] : l[2 * c];
+      const df b = P.swap ? l[2 * c] : l[2 * c + 1];
+      const float2 S = make_float2(u[2 * c].h, u[2 * c + 1].h);
+      const float2 lo = make_float2(u[2 * c].l, u[2 * c + 1].l);
+      const float2 xh = make_float2(P.neg_re ? -a.h : a.h, P.neg_im ? -b.h : b.h);
+      const float2 xl = make_float2(P.neg_re ? -a.l : a.l, P.neg_im ? -b.l : b.l);
+      const float2 s = f2_add(S, xh);
+      const float2 nbp = f2_sub(S, s);          // -bp
+      const float2 ap = f2_add(s, nbp);         // s - bp
+      const float2 db = f2_add(xh, nbp);        // xh - bp
+      const float2 da = f2_sub(S, ap);
+      float2 t = f2_add(da, db);
+      t = f2_add(t, xl);
+      const float2 lo2 = f2_add(lo, t);
+      h[2 * c] = df_norm(s.x, lo2.x);
+      h[2 * c + 1] = df_norm(s.y, lo2.y);
+    }
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const typename M::R a = P.swap ? l[2 * c + 1] : l[2 * c];
@@ -70,6 +95,20 @@ __device__ __forceinline__ void half_spinor(typename M::R* h, const typename M::
 // out += P chi for a colour vector of accumulators.
 template <class M>
 __device__ __forceinline__ void add_rebuilt(typename M::A* out, const typename M::A* chi, Phase P) {
+  if constexpr (M::kPaired) {
+    // real and imaginary parts combined in packed lanes (MathDF::combine per lane)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const DAcc a = P.swap ? chi[2 * c + 1] : chi[2 * c];
+      const DAcc b = P.swap ? chi[2 * c] : chi[2 * c + 1];
+      DAcc2 o = dacc2_get(out[2 * c], out[2 * c + 1]);
+      const DAcc2 x{make_float2(P.neg_re ? -a.S : a.S, P.neg_im ? -b.S : b.S),
+                    make_float2(P.neg_re ? -a.lo : a.lo, P.neg_im ? -b.lo : b.lo)};
+      df2_combine<1>(o, x);
+      dacc2_put(out[2 * c], out[2 * c + 1], o);
+    }
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const typename M::A a = P.swap ? chi[2 * c + 1] : chi[2 * c];
