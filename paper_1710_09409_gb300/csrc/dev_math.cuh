@@ -293,7 +293,7 @@ struct MathDFScalar : MathDF {
 // one real at a time (MathDF packs the two reals of a complex element: the
 // same values).  Measured faster for the Wilson term, whose schedule lost more
 // to the packed operations' register pairs than the packing saved (48^4:
-// 1,848 against 1,799 GB/s).
+// 1,923 against 1,887 GB/s).
 struct MathDFUnpacked : MathDF {
   static constexpr bool kPackSplit = false;
 };
