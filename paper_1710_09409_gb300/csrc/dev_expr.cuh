@@ -275,6 +275,33 @@ __device__ __forceinline__ void mm_pairs(DAcc2* P, const df* x, const df* y) {
     }
 }
 
+// Row i of mm_pairs alone: the three outputs (i, k) in P[k], each with the
+// operations mm_pairs gives it, in the same order.
+template <bool FIRST, int SG, bool AX, bool AY>
+__device__ __forceinline__ void mm_pairs_row(DAcc2* P, const df* x, const df* y, int i) {
+  constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
+  constexpr int ar = SG, ai = SG * sy, br = -SG * sx * sy, bi = SG * sx;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int xi = AX ? (3 * j + i) : (3 * i + j);
+    const df xr = x[2 * xi], xm = x[2 * xi + 1];
+    const df2 xa{make_float2(ar > 0 ? xr.h : -xr.h, ai > 0 ? xr.h : -xr.h),
+                 make_float2(ar > 0 ? xr.l : -xr.l, ai > 0 ? xr.l : -xr.l)};
+    const df2 xb{make_float2(br > 0 ? xm.h : -xm.h, bi > 0 ? xm.h : -xm.h),
+                 make_float2(br > 0 ? xm.l : -xm.l, bi > 0 ? xm.l : -xm.l)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int yi = AY ? (3 * k + j) : (3 * j + k);
+      const df yr = y[2 * yi], ym = y[2 * yi + 1];
+      const df2 ya{make_float2(yr.h, ym.h), make_float2(yr.l, ym.l)};
+      const df2 yb{make_float2(ym.h, yr.h), make_float2(ym.l, yr.l)};
+      if (FIRST && j == 0) df2_first(P[k], xa, ya);
+      else df2_fma(P[k], xa, ya);
+      df2_fma(P[k], xb, yb);
+    }
+  }
+}
+
 // z (+)= SG * op(x) * op(y), 3x3 complex; op = adjoint when AX / AY.
 template <class M, bool FIRST, int SG, bool AX, bool AY>
 __device__ __forceinline__ void mm_acc(typename M::A* z, const typename M::R* x,

@@ -523,6 +523,85 @@ struct TwoProducts<Add<X, Y>> : TwoProductsOf<X, Y, 1> {};
 template <class X, class Y>
 struct TwoProducts<Sub<X, Y>> : TwoProductsOf<X, Y, -1> {};
 
+// Sums and differences of two 3x3 products whose leaves overlap
+// (adj(a)*b - b*adj(a)): every leaf stays live through both products, so the
+// whole-tile kernel evaluates the output one row at a time -- the first
+// product's row into three accumulators, the second's row combined into them,
+// the row converted and stored -- and holds three outputs' accumulators
+// instead of the eighteen of both products.  Each output's operations are
+// acc_node's and mul_combine's in the same order: the values are unchanged.
+// Pair arithmetic with packed (re, im) lanes, full FP64 matrices.
+template <class T>
+struct MatLeafOperand {
+  static constexpr bool value = false;
+};
+template <int J>
+struct MatLeafOperand<LM<J>> {
+  static constexpr bool value = true, adj = false;
+  static constexpr int slot = J;
+};
+template <int J>
+struct MatLeafOperand<Adj<LM<J>>> {
+  static constexpr bool value = true, adj = true;
+  static constexpr int slot = J;
+};
+template <class T>
+struct MatLeafProduct {
+  static constexpr bool value = false;
+};
+template <class X, class Y>
+struct MatLeafProduct<Mul<X, Y>> {
+  using LX = MatLeafOperand<X>;
+  using LY = MatLeafOperand<Y>;
+  static constexpr bool value = LX::value && LY::value;
+};
+template <class T>
+struct RowProducts {
+  static constexpr bool value = false;
+};
+template <class X, class Y, int SG>
+struct RowProductsOf {
+  static constexpr bool value =
+      MatLeafProduct<X>::value && MatLeafProduct<Y>::value && !disjoint_leaves<X, Y, 0>();
+  using P0 = MatLeafProduct<X>;
+  using P1 = MatLeafProduct<Y>;
+  static constexpr int S1 = SG;
+};
+template <class X, class Y>
+struct RowProducts<Add<X, Y>> : RowProductsOf<X, Y, 1> {};
+template <class X, class Y>
+struct RowProducts<Sub<X, Y>> : RowProductsOf<X, Y, -1> {};
+
+template <class Tree, class M, int PREC>
+struct RowProductsOk {
+  static constexpr bool value = RowProducts<Tree>::value && M::kPaired && PREC == P_F64;
+};
+
+// Evaluate and store site s, row by row (RowProductsOk holds).
+template <class Tree, class M, class C>
+__device__ __forceinline__ void row_products_store(const FieldDesc& f, const C& ctx, int64_t s,
+                                                   int mu) {
+  using RP = RowProducts<Tree>;
+  using X0 = typename RP::P0::LX;
+  using Y0 = typename RP::P0::LY;
+  using X1 = typename RP::P1::LX;
+  using Y1 = typename RP::P1::LY;
+  const int64_t b = elem_base(f, s, mu);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    DAcc2 P[3], Q[3];
+    mm_pairs_row<true, 1, X0::adj, Y0::adj>(P, ctx.leaf[X0::slot], ctx.leaf[Y0::slot], i);
+    mm_pairs_row<true, 1, X1::adj, Y1::adj>(Q, ctx.leaf[X1::slot], ctx.leaf[Y1::slot], i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      df2_combine<RP::S1>(P[k], Q[k]);
+      typename M::A re, im;
+      dacc2_put(re, im, P[k]);
+      Store<P_F64>::template store_acc<M>(f.ptr, b + (3 * i + k) * f.s_c, &re, &im);
+    }
+  }
+}
+
 // Read the staged leaves of subtree Sub (this lane's site) into ctx.
 template <class Tree, class Sub, int I, int PREC, class M, class C>
 __device__ __forceinline__ void read_leaves_of(const unsigned char* buf, int lane, C& ctx) {
@@ -565,6 +644,18 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
     phase ^= 1;
     ctx.gmax = p.gscal;
     const int64_t tn = t + wstride;
+    if constexpr (RowProductsOk<Tree, M, PREC>::value) {
+      read_leaves<Tree, 0, PREC, M>(buf, lane, ctx);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (tn < ntiles) issue_tile<Tree, PREC, false>(lane, p, nullptr, nullptr, tn << 5, mu, buf, bar);
+      if (M::kGuard && __any_sync(0xffffffffu, guard_trips<Tree>(ctx.gmax)))
+        eval_site_f64<Tree, PREC>(p, (t << 5) + lane, mu);
+      else
+        row_products_store<Tree, M>(p.dst, ctx, (t << 5) + lane, mu);
+      t = tn;
+      continue;
+    }
     if constexpr (TwoProducts<Tree>::value) {
       using TP = TwoProducts<Tree>;
       typename M::A acc[1][W];
@@ -608,8 +699,10 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
   }
 }
 
+// Row-by-row products fit 128 registers: two blocks of 256 threads per SM.
 template <class Tree, class M, int PREC>
-__global__ void __launch_bounds__(256) k_eval_tma(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(256, RowProductsOk<Tree, M, PREC>::value ? 2 : 1)
+    k_eval_tma(const __grid_constant__ KParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (!smem_aligned(smem, p.err)) return;
   tma_range<Tree, M, PREC>(p, warp_range(p.nvec >> 5), smem);

@@ -220,7 +220,11 @@ struct MathDF {
   __device__ static __forceinline__ void fma(A& a, const R& x0, const R& y) {
     const float xh = SG > 0 ? x0.h : -x0.h;
     const float xl = SG > 0 ? x0.l : -x0.l;
-    const float p = __fmul_rn(xh, y.h);
+    // The leading product is rounded toward zero: TwoSum below is exact for
+    // any float p, and xh*yh - p is exact in one FMA for a truncated product
+    // as for a rounded one.  (The packed form, mul.rz.f32x2, cannot be merged
+    // into the round-to-nearest add that follows it.)
+    const float p = __fmul_rz(xh, y.h);
     if (FIRST) {
       float q = __fmaf_rn(xh, y.h, -p);       // exact error of the leading product
       q = __fmaf_rn(xh, y.l, q);
@@ -304,14 +308,13 @@ struct MathDFUnpacked : MathDF {
 // operations per issued instruction).  Each lane performs exactly the
 // operations of MathDF::fma / MathDF::combine in the same order, so the packed
 // path gives the same values as the scalar one.  Adds, subtracts and FMAs are
-// packed (PTX with an explicit round-to-nearest-even modifier); the leading
-// products stay two scalar multiplies.  With CUDA 13.0 on sm_103a a packed
-// multiply whose result feeds a packed add lost TwoSum's exact error term (the
-// 3x3 product came out with FP32 accuracy, ~1e-8), while scalar multiplies
-// with packed adds, or packed multiplies with scalar adds, gave the scalar
-// arithmetic's values; the scalar multiplies cost one instruction more per
-// term.  -bp is formed as S - s, the exact negation of s - S under
-// round-to-nearest-even.
+// packed (PTX with an explicit round-to-nearest-even modifier), and so is the
+// leading product, rounded toward zero (mul.rz.f32x2).  With CUDA 13.0 on
+// sm_103a a packed round-to-nearest multiply whose result fed a packed add
+// was merged with it into one FMA, which loses TwoSum's exact error term (the
+// 3x3 product came out with FP32 accuracy, ~1e-8); a truncated product cannot
+// be merged into a rounded add.  -bp is formed as S - s, the exact negation of
+// s - S under round-to-nearest-even.
 struct DAcc2 {
   float2 S, lo;  // .x = real part's accumulator, .y = imaginary part's
 };
@@ -319,9 +322,13 @@ struct df2 {
   float2 h, l;   // lane-wise leading and trailing parts
 };
 
-// lane-wise product as two scalar multiplies (see above)
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
-  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+// lane-wise leading product x.h * y.h rounded toward zero (MathDF::fma's p)
+__device__ __forceinline__ float2 f2_mul_lead(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rz.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 __device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
   float2 d;
@@ -359,8 +366,8 @@ __device__ __forceinline__ void dacc2_put(DAcc& re, DAcc& im, const DAcc2& a) {
 
 // a = x * y lane-wise (MathDF::fma with FIRST)
 __device__ __forceinline__ void df2_first(DAcc2& a, const df2& x, const df2& y) {
-  const float2 p = f2_mul(x.h, y.h);
-  const float2 np = f2_mul(p, make_float2(-1.0f, -1.0f));  // -p, exact
+  const float2 p = f2_mul_lead(x.h, y.h);
+  const float2 np = make_float2(-p.x, -p.y);
   float2 q = f2_fma(x.h, y.h, np);            // exact error of the leading product
   q = f2_fma(x.h, y.l, q);
   q = f2_fma(x.l, y.h, q);
@@ -370,7 +377,7 @@ __device__ __forceinline__ void df2_first(DAcc2& a, const df2& x, const df2& y) 
 
 // a += x * y lane-wise (MathDF::fma without FIRST)
 __device__ __forceinline__ void df2_fma(DAcc2& a, const df2& x, const df2& y) {
-  const float2 p = f2_mul(x.h, y.h);
+  const float2 p = f2_mul_lead(x.h, y.h);
   const float2 s = f2_add(a.S, p);            // TwoSum(S, xh*yh)
   const float2 nbp = f2_sub(a.S, s);          // -bp
   const float2 ap = f2_add(s, nbp);           // s - bp

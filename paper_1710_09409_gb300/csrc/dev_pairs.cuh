@@ -47,7 +47,7 @@ __device__ __forceinline__ float2 f2_neg(float2 a) { return make_float2(-a.x, -a
 // even is symmetric), so the negative form negates the two results.
 template <bool NEG>
 __device__ __forceinline__ void dp_first(dpa& a, const dp& x, const dp& y) {
-  const float2 p = f2_mul(x.h, y.h);
+  const float2 p = f2_mul_lead(x.h, y.h);
   const float2 np = f2_neg(p);
   float2 q = f2_fma(x.h, y.h, np);  // exact error of the leading product
   q = f2_fma(x.h, y.l, q);
@@ -66,7 +66,7 @@ __device__ __forceinline__ void dp_first(dpa& a, const dp& x, const dp& y) {
 // error terms come out negated (c = -db, u = -t) and enter by subtraction.
 template <bool NEG>
 __device__ __forceinline__ void dp_fma(dpa& a, const dp& x, const dp& y) {
-  const float2 p = f2_mul(x.h, y.h);
+  const float2 p = f2_mul_lead(x.h, y.h);
   if (!NEG) {
     const float2 s = f2_add(a.S, p);        // TwoSum(S, xh*yh)
     const float2 nbp = f2_sub(a.S, s);      // -bp
