@@ -220,11 +220,11 @@ struct MathDF {
   __device__ static __forceinline__ void fma(A& a, const R& x0, const R& y) {
     const float xh = SG > 0 ? x0.h : -x0.h;
     const float xl = SG > 0 ? x0.l : -x0.l;
-    // The leading product is rounded toward zero: TwoSum below is exact for
-    // any float p, and xh*yh - p is exact in one FMA for a truncated product
-    // as for a rounded one.  (The packed form, mul.rz.f32x2, cannot be merged
-    // into the round-to-nearest add that follows it.)
-    const float p = __fmul_rz(xh, y.h);
+    // The leading product is formed as xh*yh + (+0): the rounded product,
+    // except that an exact -0 comes out as +0 (TwoSum below is exact for any
+    // float p).  Its packed form, fma.rn.f32x2 with a +0 addend, is not a
+    // plain multiply, which the compiler would merge into the add after it.
+    const float p = __fmaf_rn(xh, y.h, 0.0f);
     if (FIRST) {
       float q = __fmaf_rn(xh, y.h, -p);       // exact error of the leading product
       q = __fmaf_rn(xh, y.l, q);
@@ -309,12 +309,13 @@ struct MathDFUnpacked : MathDF {
 // operations of MathDF::fma / MathDF::combine in the same order, so the packed
 // path gives the same values as the scalar one.  Adds, subtracts and FMAs are
 // packed (PTX with an explicit round-to-nearest-even modifier), and so is the
-// leading product, rounded toward zero (mul.rz.f32x2).  With CUDA 13.0 on
-// sm_103a a packed round-to-nearest multiply whose result fed a packed add
-// was merged with it into one FMA, which loses TwoSum's exact error term (the
-// 3x3 product came out with FP32 accuracy, ~1e-8); a truncated product cannot
-// be merged into a rounded add.  -bp is formed as S - s, the exact negation of
-// s - S under round-to-nearest-even.
+// leading product, as an FMA with a +0 addend.  With CUDA 13.0 on sm_103a a
+// packed multiply whose result fed a packed add was merged with it into one
+// FMA, which loses TwoSum's exact error term (the 3x3 product came out with
+// FP32 accuracy, ~1e-8), and so was an FMA with a -0 addend (exactly a
+// multiply); an FMA with a +0 addend differs from a multiply for a -0 product
+// and is kept apart.  -bp is formed as S - s, the exact negation of s - S
+// under round-to-nearest-even.
 struct DAcc2 {
   float2 S, lo;  // .x = real part's accumulator, .y = imaginary part's
 };
@@ -322,11 +323,11 @@ struct df2 {
   float2 h, l;   // lane-wise leading and trailing parts
 };
 
-// lane-wise leading product x.h * y.h rounded toward zero (MathDF::fma's p)
+// lane-wise leading product x.h * y.h + (+0) (MathDF::fma's p)
 __device__ __forceinline__ float2 f2_mul_lead(float2 a, float2 b) {
   float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rz.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, 0;\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
       : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
   return d;
 }
