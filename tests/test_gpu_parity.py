@@ -214,6 +214,47 @@ def test_fused_trees(su3s, name, tree, lay, math):
     assert np.abs(z.download() - ref).max() < TOL * 2
 
 
+COMM = ("sub", ("mul", ("leaf", "a"), ("leaf", "b")), ("mul", ("leaf", "b"), ("leaf", "a")))
+
+
+@pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
+def test_commutator_tree(su3s, math):
+    """a*b - b*a, a catalogued tree whose two products share both leaves (the
+    staged kernel forms its output row by row): every data movement gives the
+    same bits, the oracle's value within the bound, a traceless result (the
+    trace of a commutator vanishes), and exactly zero when b is the identity
+    (both products then combine the same values)."""
+    dims = (8, 8, 8, 9)
+    lat = su3s.Lattice(dims)
+    f = lattice_fields(dims, SEED, names=("a", "b"))
+    a, b = (upload(su3s, lat, f[n]) for n in "ab")
+    e = a * b - b * a
+    assert e.signature() in {s for (_, s, p, m) in su3s.catalogue() if p == "f64"}
+    outs = []
+    try:
+        for mode in (su3s.PIPE_PLAIN, su3s.PIPE_TMA, su3s.PIPE_TMA_LEAF, su3s.PIPE_TMA_RING,
+                     su3s.PIPE_TMA_PAIR):
+            su3s.set_pipeline(mode)
+            z = a.like()
+            su3s.evaluate(z, e, math)
+            outs.append(z.download())
+    finally:
+        su3s.set_pipeline(su3s.PIPE_AUTO)
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    ref = oracle.eval_tree(COMM, f)
+    assert np.abs(outs[0] - ref).max() < 2 * TOL
+    tr = cplx(outs[0])[:, [0, 1, 2], [0, 1, 2]].sum(axis=1)
+    assert np.abs(tr).max() < 2 * TOL
+    eye = np.zeros_like(f["a"])
+    eye[:, [0, 1, 2], [0, 1, 2], 0] = 1.0
+    i = upload(su3s, lat, eye)
+    z = a.like()
+    su3s.evaluate(z, a * i - i * a, math)
+    assert np.array_equal(z.download() + 0.0, np.zeros_like(eye))
+    assert su3s.device_error() == 0
+
+
 @pytest.mark.parametrize("math", MATHS, ids=MATH_IDS)
 def test_fused_equals_term_by_term_on_gpu(su3s, math):
     dims = (8, 8, 8, 8)
