@@ -44,7 +44,9 @@ __device__ __forceinline__ float2 f2_neg(float2 a) { return make_float2(-a.x, -a
 
 // a = +x*y (NEG: -x*y), MathDF::fma with FIRST.  With x negated every value of
 // the sequence is the exact negation of the positive one (round to nearest
-// even is symmetric), so the negative form negates the two results.
+// even is symmetric), so the negative form negates the two results.  Zeros
+// are the exception (the leading product's +0 addend turns a -0 product into
+// +0): a result may differ from MathDF's in the sign of a zero, never in value.
 template <bool NEG>
 __device__ __forceinline__ void dp_first(dpa& a, const dp& x, const dp& y) {
   const float2 p = f2_mul_lead(x.h, y.h);
@@ -63,7 +65,8 @@ __device__ __forceinline__ void dp_first(dpa& a, const dp& x, const dp& y) {
 
 // a += x*y (NEG: a -= x*y), MathDF::fma without FIRST, lane-wise.  The
 // negative form is MathDF's sequence for -x written with x: s = S - p, the
-// error terms come out negated (c = -db, u = -t) and enter by subtraction.
+// error terms come out negated (c = -db, u = -t) and enter by subtraction
+// (equal values; the sign of a zero may differ, as in dp_first).
 template <bool NEG>
 __device__ __forceinline__ void dp_fma(dpa& a, const dp& x, const dp& y) {
   const float2 p = f2_mul_lead(x.h, y.h);
