@@ -275,29 +275,60 @@ __device__ __forceinline__ void mm_pairs(DAcc2* P, const df* x, const df* y) {
     }
 }
 
-// Row i of mm_pairs alone: the three outputs (i, k) in P[k], each with the
-// operations mm_pairs gives it, in the same order.
-template <bool FIRST, int SG, bool AX, bool AY>
-__device__ __forceinline__ void mm_pairs_row(DAcc2* P, const df* x, const df* y, int i) {
+// Operand pairs of mm_pairs for SG = +1: x element (i, j) of op(x) with the
+// signs of the two terms, y element (j, k) of op(y) and its swapped copy.
+template <bool AX, bool AY>
+__device__ __forceinline__ df2 row_xa(const df* x, int i, int j) {
+  constexpr int ai = AY ? -1 : 1;
+  const int xi = AX ? (3 * j + i) : (3 * i + j);
+  const df xr = x[2 * xi];
+  return df2{make_float2(xr.h, ai > 0 ? xr.h : -xr.h), make_float2(xr.l, ai > 0 ? xr.l : -xr.l)};
+}
+template <bool AX, bool AY>
+__device__ __forceinline__ df2 row_xb(const df* x, int i, int j) {
   constexpr int sx = AX ? -1 : 1, sy = AY ? -1 : 1;
-  constexpr int ar = SG, ai = SG * sy, br = -SG * sx * sy, bi = SG * sx;
+  constexpr int br = -sx * sy, bi = sx;
+  const int xi = AX ? (3 * j + i) : (3 * i + j);
+  const df xm = x[2 * xi + 1];
+  return df2{make_float2(br > 0 ? xm.h : -xm.h, bi > 0 ? xm.h : -xm.h),
+             make_float2(br > 0 ? xm.l : -xm.l, bi > 0 ? xm.l : -xm.l)};
+}
+template <bool AY>
+__device__ __forceinline__ df2 row_ya(const df* y, int j, int k) {
+  const int yi = AY ? (3 * k + j) : (3 * j + k);
+  const df yr = y[2 * yi], ym = y[2 * yi + 1];
+  return df2{make_float2(yr.h, ym.h), make_float2(yr.l, ym.l)};
+}
+template <bool AY>
+__device__ __forceinline__ df2 row_yb(const df* y, int j, int k) {
+  const int yi = AY ? (3 * k + j) : (3 * j + k);
+  const df yr = y[2 * yi], ym = y[2 * yi + 1];
+  return df2{make_float2(ym.h, yr.h), make_float2(ym.l, yr.l)};
+}
+
+// Rows i of two products at once, P[k] = row i of op(x0) op(y0) and Q[k] = row i
+// of op(x1) op(y1), their terms interleaved; each output receives mm_pairs'
+// operations in mm_pairs' order.
+template <bool AX0, bool AY0, bool AX1, bool AY1>
+__device__ __forceinline__ void mm_pairs_row2(DAcc2* P, DAcc2* Q, const df* x0, const df* y0,
+                                              const df* x1, const df* y1, int i) {
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const int xi = AX ? (3 * j + i) : (3 * i + j);
-    const df xr = x[2 * xi], xm = x[2 * xi + 1];
-    const df2 xa{make_float2(ar > 0 ? xr.h : -xr.h, ai > 0 ? xr.h : -xr.h),
-                 make_float2(ar > 0 ? xr.l : -xr.l, ai > 0 ? xr.l : -xr.l)};
-    const df2 xb{make_float2(br > 0 ? xm.h : -xm.h, bi > 0 ? xm.h : -xm.h),
-                 make_float2(br > 0 ? xm.l : -xm.l, bi > 0 ? xm.l : -xm.l)};
+    const df2 xa0 = row_xa<AX0, AY0>(x0, i, j), xb0 = row_xb<AX0, AY0>(x0, i, j);
+    const df2 xa1 = row_xa<AX1, AY1>(x1, i, j), xb1 = row_xb<AX1, AY1>(x1, i, j);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const int yi = AY ? (3 * k + j) : (3 * j + k);
-      const df yr = y[2 * yi], ym = y[2 * yi + 1];
-      const df2 ya{make_float2(yr.h, ym.h), make_float2(yr.l, ym.l)};
-      const df2 yb{make_float2(ym.h, yr.h), make_float2(ym.l, yr.l)};
-      if (FIRST && j == 0) df2_first(P[k], xa, ya);
-      else df2_fma(P[k], xa, ya);
-      df2_fma(P[k], xb, yb);
+      const df2 ya0 = row_ya<AY0>(y0, j, k), yb0 = row_yb<AY0>(y0, j, k);
+      const df2 ya1 = row_ya<AY1>(y1, j, k), yb1 = row_yb<AY1>(y1, j, k);
+      if (j == 0) {
+        df2_first(P[k], xa0, ya0);
+        df2_first(Q[k], xa1, ya1);
+      } else {
+        df2_fma(P[k], xa0, ya0);
+        df2_fma(Q[k], xa1, ya1);
+      }
+      df2_fma(P[k], xb0, yb0);
+      df2_fma(Q[k], xb1, yb1);
     }
   }
 }

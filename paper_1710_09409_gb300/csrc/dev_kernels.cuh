@@ -590,8 +590,8 @@ __device__ __forceinline__ void row_products_store(const FieldDesc& f, const C& 
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     DAcc2 P[3], Q[3];
-    mm_pairs_row<true, 1, X0::adj, Y0::adj>(P, ctx.leaf[X0::slot], ctx.leaf[Y0::slot], i);
-    mm_pairs_row<true, 1, X1::adj, Y1::adj>(Q, ctx.leaf[X1::slot], ctx.leaf[Y1::slot], i);
+    mm_pairs_row2<X0::adj, Y0::adj, X1::adj, Y1::adj>(P, Q, ctx.leaf[X0::slot], ctx.leaf[Y0::slot],
+                                                      ctx.leaf[X1::slot], ctx.leaf[Y1::slot], i);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       df2_combine<RP::S1>(P[k], Q[k]);
