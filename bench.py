@@ -108,7 +108,7 @@ TRAFFIC_32 = {
     "k_eval_tma<Mul<LM<0>, LV<1>>, MathDF, 0>": (228.6 * 1e6, 251658240),
     "k_eval_tma<Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>, MathDF, 0>": (729.2 * 1e6, 754974720),
     "k_eval_tma<Add<Mul<Mul<LM<0>, LM<1>>, LM<2>>, Scale<0, LM<3>>>, MathDF, 0>": (728.5 * 1e6, 754974720),
-    "k_eval_tma<Sub<Mul<Adj<LM<0>>, LM<1>>, Mul<LM<1>, Adj<LM<0>>>>, MathDF, 0>": (412.7 * 1e6, 452984832),
+    "k_eval_tma<Sub<Mul<Adj<LM<0>>, LM<1>>, Mul<LM<1>, Adj<LM<0>>>>, MathDF, 0>": (414.7 * 1e6, 452984832),
     "k_eval_tma<Mul<LM<0>, LM<1>>, MathDF, 4>": (265.2 * 1e6, 301989888),
     "k_batch_tma<MathDF, Add<Mul<LM<0>, LM<1>>, Mul<LM<2>, LM<3>>>>": (4602.2 * 1e6, 4622376960),
     "k_adjoint_tma<Mul<LM<0>, LM<1>>, MathDF>": (703.6 * 1e6, 754974720),
