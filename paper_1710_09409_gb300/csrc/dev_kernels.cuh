@@ -699,9 +699,22 @@ __device__ __forceinline__ void tma_range(const KParams& p, Range rg, unsigned c
   }
 }
 
-// Row-by-row products fit 128 registers: two blocks of 256 threads per SM.
+// Minimum blocks per SM the whole-tile kernel declares, which steers the
+// registers ptxas gives it: row-by-row products fit 128 registers (two blocks
+// of 256 threads); the other full-matrix trees in the pair arithmetic are given
+// the registers of one block (more independent work per warp: a*b+c*d 234
+// instead of 186 registers at the same 8 warps per SM, and measured faster);
+// two-row matrices and the other arithmetics state no minimum (two-row a*b: 107
+// registers and many warps, 10% faster than with one block's 148).
 template <class Tree, class M, int PREC>
-__global__ void __launch_bounds__(256, RowProductsOk<Tree, M, PREC>::value ? 2 : 1)
+struct TmaMinBlocks {
+  static constexpr int value = RowProductsOk<Tree, M, PREC>::value        ? 2
+                               : (PREC == P_F64 && M::kPaired) ? 1
+                                                                : 0;
+};
+
+template <class Tree, class M, int PREC>
+__global__ void __launch_bounds__(256, TmaMinBlocks<Tree, M, PREC>::value)
     k_eval_tma(const __grid_constant__ KParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (!smem_aligned(smem, p.err)) return;
