@@ -608,7 +608,7 @@ struct MathF32 {
 
 // ------------------------------------------ complex elements, two reals
 // Packed product, used only where it feeds another product: a packed
-// multiply feeding a packed add is not kept apart from it (see f2_mul).
+// multiply feeding a packed add is not kept apart from it (see f2_mul_lead).
 __device__ __forceinline__ float2 f2_mul_packed(float2 a, float2 b) {
   float2 d;
   asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
