@@ -201,6 +201,24 @@ def test_fused_trees_equal_term_by_term():
     assert np.abs(np.trace(e3, axis1=1, axis2=2)).max() < 1e-13
 
 
+def test_commutator_tree():
+    """a*b - b*a: numpy's matrix products, a vanishing trace (tr(ab) = tr(ba)),
+    and exactly zero when b is the identity or when b = a."""
+    dims = (3, 2, 1, 5)
+    f = lattice_fields(dims, SEED, names=("a", "b"))
+    comm = ("sub", ("mul", ("leaf", "a"), ("leaf", "b")), ("mul", ("leaf", "b"), ("leaf", "a")))
+    ca, cb = cplx(f["a"]), cplx(f["b"])
+    z = cplx(oracle.eval_tree(comm, f))
+    assert np.abs(z - (ca @ cb - cb @ ca)).max() < 1e-14
+    assert np.abs(np.trace(z, axis1=1, axis2=2)).max() < 1e-14
+    eye = np.zeros_like(f["a"])
+    eye[:, [0, 1, 2], [0, 1, 2], 0] = 1.0
+    zi = oracle.eval_tree(comm, {"a": f["a"], "b": eye})
+    assert np.array_equal(zi + 0.0, np.zeros_like(eye))
+    za = oracle.eval_tree(comm, {"a": f["a"], "b": f["a"]})
+    assert np.array_equal(za + 0.0, np.zeros_like(eye))
+
+
 def test_ill_typed_trees_are_rejected():
     f = lattice_fields((1, 1, 1, 1), SEED, names=("a", "v"))
     with pytest.raises(ValueError):
